@@ -1,0 +1,48 @@
+"""The seeded generators produce the documented shapes, windows and partitions."""
+import numpy as np
+
+from workloads import (make_grid_ls, config_tiny, block_partition, strip_partition,
+                       bisection_partition, config_batch_sizes)
+
+
+def test_tiny_shape(tiny):
+    assert (tiny.m, tiny.n, tiny.nnz, tiny.nparts) == (5120, 1024, 17408, 8)
+    assert np.all(np.diff(tiny.row_ptr) > 0)
+    # strips of 32x4
+    assert np.all(np.bincount(tiny.part) == 128)
+
+
+def test_rows_lie_in_windows_and_are_sorted():
+    W, H, r, k = 20, 17, 3, 8
+    m, n, rp, c, v, b, _ = make_grid_ls(W, H, 4, k, r, 5)
+    mr = 4 * n
+    cols = c[: mr * k].reshape(mr, k).astype(np.int64)
+    assert np.all(np.diff(cols, axis=1) > 0)  # distinct, ascending
+    gx, gy = cols % W, cols // W
+    assert np.all(gx.max(1) - gx.min(1) <= 2 * r) and np.all(gy.max(1) - gy.min(1) <= 2 * r)
+    assert np.all(c[mr * k:] == np.arange(n)) and np.all(v[mr * k:] == 1e-2)
+    assert b.shape == (m,)
+
+
+def test_determinism_and_chunking():
+    a = make_grid_ls(30, 30, 4, 8, 3, 1)
+    b = make_grid_ls(30, 30, 4, 8, 3, 1)
+    for x, y in zip(a[2:6], b[2:6]):
+        assert np.array_equal(x, y)
+
+
+def test_partitions():
+    p = block_partition(1024, 1024, 64, 64)
+    assert p.max() == 255 and np.all(np.bincount(p) == 4096)
+    assert p[0] == 0 and p[64] == 1 and p[64 * 1024] == 16
+    s = strip_partition(32, 32, 4)
+    assert s[128] == 1
+    q = bisection_partition(200, 180, 8192, 3)
+    sizes = np.bincount(q)
+    assert sizes.max() <= 8192 and sizes.min() > 1000
+
+
+def test_batch_sizes():
+    sides = config_batch_sizes()
+    assert len(sides) == 64
+    assert min(s * s for s in sides) >= 16000 and max(s * s for s in sides) <= 263000
