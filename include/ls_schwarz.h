@@ -1,0 +1,192 @@
+/*
+ * ls_schwarz.h -- C ABI of a GB300 (sm_103a) solver for sparse linear least squares
+ *
+ *     min_x || A x - b ||_2,   A in R^{m x n}, m >= n,
+ *
+ * by conjugate gradients on the normal equations C x = A^T b, C = A^T A (eq. (1.2)
+ * of Al Daas, Jolivet & Scott, arXiv 2107.09006), preconditioned by the two-level
+ * additive Schwarz preconditioner of eq. (2.3):
+ *
+ *     M^{-1} = R_0^T C_00^{-1} R_0 + sum_i R_i^T C_ii^{-1} R_i,
+ *
+ * with overlapping subdomains Omega_i = [Omega_I,i, Omega_Gamma,i] built from the
+ * rows Xi_i of A that touch the interior columns (Section 3), local matrices
+ * C_ii = A(:,Omega_i)^T A(:,Omega_i) (Section 3.1), the local SPSD splittings
+ * C~_ii = A(Xi_i,Omega_i)^T A(Xi_i,Omega_i) (eq. (3.2)), and a coarse space from the
+ * shifted generalized eigenproblems D_i C_ii D_i v = lambda (C~_ii + s I) v with
+ * threshold tau (eqs. (3.4)-(3.6), Algorithm 1).  C is never formed in the solve:
+ * it is applied as A^T (A p) (Section 4.1.3).
+ *
+ * Conventions shared by every call:
+ *  - Pointers may be host or device memory (the library inspects each one); the
+ *    caller owns every pointer it passes and may free it after the call returns.
+ *  - Index arrays are 0-based.  CSR column indices must be strictly increasing
+ *    within each row (no duplicates); "nonzero" means "stored", as in Section 3.
+ *  - Every call returns an ls_status; on failure ls_last_error() gives a message
+ *    (thread-local, valid until the next call from the same thread) and no output
+ *    is to be trusted, but the handle stays valid for ls_free.
+ *  - Calls are synchronous with respect to their outputs: when a call returns,
+ *    its outputs are written (device outputs are complete on the handle's stream).
+ *  - All device work of a handle runs on one CUDA stream on the device that was
+ *    current at ls_setup; calls on one handle must not overlap.
+ */
+#ifndef LS_SCHWARZ_H
+#define LS_SCHWARZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LS_OK = 0,
+    LS_ERR_INVALID = 1,        /* bad argument: sizes, CSR structure, partition ids     */
+    LS_ERR_OOM = 2,            /* device or host allocation failed                      */
+    LS_ERR_CUDA = 3,           /* a CUDA runtime call failed                            */
+    LS_ERR_FACTOR = 4,         /* a local or coarse Cholesky met a pivot <= 0           */
+    LS_ERR_EIGEN = 5,          /* a local eigensolve did not converge                   */
+    LS_ERR_NOT_CONVERGED = 6,  /* maxit reached before the residual test passed         */
+    LS_ERR_NONFINITE = 7,      /* NaN or Inf met in the input or in a CG scalar         */
+    LS_ERR_DEVICE_TIMEOUT = 8, /* a bounded device-side wait gave up                    */
+    LS_ERR_UNSUPPORTED = 9     /* valid request outside what this build implements     */
+} ls_status;
+
+typedef enum {
+    LS_PREC_F64 = 0,  /* local factors and triangular solves in FP64 (plain CG)             */
+    LS_PREC_F32 = 1,  /* local factors in FP32, FP64 outer flexible CG                      */
+    LS_PREC_BF16 = 2  /* local factors in BF16 with one FP32 scale per 32x32 tile, FP32
+                         accumulation, FP64 outer flexible CG                               */
+} ls_precision;
+
+typedef struct {
+    double tau;        /* eigenvalue threshold: keep lambda > 1/tau (Lemma 2.4).  tau <= 0
+                          selects it automatically: 1/tau = max_i lambda_{i, nev_max+1},
+                          so no subdomain keeps more than nev_max vectors.             */
+    int nev_max;       /* most coarse vectors per subdomain (Section 4 uses 300)       */
+    double delta_rel;  /* construction shift delta = delta_rel ||C||_F (Section 4.1.2) */
+    double s_rel;      /* GEVP shift s_i = s_rel ||C~_ii||_F (Section 4.1.2)           */
+    int factor_prec;   /* ls_precision                                                  */
+    int maxit;         /* CG iteration limit                                            */
+    int coarse;        /* 1: two-level additive (eq. (2.3)); 0: one-level ASM (eq. (2.1)) */
+    int fixed_iters;   /* > 0: run exactly this many CG iterations, no residual test    */
+    int eig_maxit;     /* limit on Lanczos steps per subdomain eigensolve               */
+    double eig_tol;    /* relative Ritz residual tolerance of the eigensolve           */
+    int use_graph;     /* 1: replay each CG iteration as a captured CUDA graph          */
+} ls_options;
+
+typedef struct {
+    int iters;               /* CG iterations of the last solve                            */
+    int restarts;            /* restarts from the true residual                            */
+    double relres_recursive; /* ||r_k|| / ||A^T b|| of the recursion at exit               */
+    double relres_true;      /* ||A^T (b - A x)|| / ||A^T b|| recomputed at exit           */
+    double kappa_lanczos;    /* condition estimate of M^{-1} C from the CG coefficients     */
+    int n0;                  /* coarse dimension sum_i k_i                                  */
+    int kmin, kmax;          /* fewest / most coarse vectors of one subdomain              */
+    double tau_used;         /* the threshold tau actually applied                          */
+    double delta;            /* the construction shift delta                                */
+    double t_setup;          /* seconds: whole ls_setup                                     */
+    double t_eig;            /* seconds: the local eigensolves                              */
+    double t_solve;          /* seconds: the last ls_solve / ls_backward                    */
+    int bad_subdomain;       /* subdomain of a factor / eigen failure, else -1              */
+    int eig_steps_max;       /* most Lanczos steps one subdomain needed                     */
+} ls_info;
+
+typedef struct ls_handle ls_handle;
+
+/* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
+ * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
+ * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1. */
+void ls_default_options(ls_options* opt);
+
+/* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping
+ * column partition.
+ *   m, n            rows and columns of A (m >= 1, n >= 1)
+ *   row_ptr[m+1]    int64 CSR row offsets; col[nnz] int32; val[nnz] float64
+ *   nparts          number N of subdomains (1 <= N <= n)
+ *   part[n]         int32 subdomain id of every column (the sets Omega_I,i)
+ *   overlap         must be 1 (Omega_Gamma,i = distance one in G(C), Section 2);
+ *                   any other value returns LS_ERR_UNSUPPORTED
+ *   opt             options (NULL: defaults)
+ *   stream          cudaStream_t the handle uses (NULL: the handle creates its own)
+ *   out             receives the handle
+ * The index sets are built on the host; local matrices, their Cholesky factors,
+ * the eigensolves and the coarse operator are built on the device.  A and the
+ * partition are copied: the caller may free them afterwards.
+ * Errors: LS_ERR_INVALID (sizes, unsorted or out-of-range indices, part out of
+ * range, non-finite values), LS_ERR_FACTOR (info via ls_handle_info), LS_ERR_EIGEN,
+ * LS_ERR_OOM, LS_ERR_CUDA. */
+ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                   const double* val, int32_t nparts, const int32_t* part, int overlap,
+                   const ls_options* opt, void* stream, ls_handle** out);
+
+/* Solve min ||A x - b|| for nrhs right-hand sides by PCG on C x = A^T b with x_0 = 0.
+ *   b[m * nrhs]     column-major right-hand sides (host or device)
+ *   rtol            stop when ||A^T (b - A x)|| <= rtol ||A^T b|| (true residual,
+ *                   recomputed whenever the recursive residual passes the test; if
+ *                   the true one fails, CG restarts from it)
+ *   x[n * nrhs]     output, column-major (host or device)
+ *   info            statistics of the last right-hand side (may be NULL)
+ * Errors: LS_ERR_NOT_CONVERGED (x holds the last iterate), LS_ERR_NONFINITE. */
+ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x,
+                   ls_info* info);
+
+/* Reverse mode of x(A, b) = C^{-1} A^T b.  With lambda = C^{-1} grad_x solved by the
+ * same preconditioned CG to rtol:
+ *   grad_b = A lambda                                   (m entries per right-hand side)
+ *   grad_vals[k] = rho_r lambda_c - (A lambda)_r x_c    for CSR entry k = (r, c),
+ *                  rho = b - A x                        (summed over right-hand sides)
+ * b, x, grad_x are the forward inputs/outputs (column-major, host or device);
+ * grad_b or grad_vals may be NULL to skip them. */
+ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x,
+                      int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void ls_free(ls_handle* h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ls_last_error(void);
+
+/* Setup statistics (n0, k range, tau, delta, times, failing subdomain). */
+ls_status ls_handle_info(const ls_handle* h, ls_info* info);
+
+/* ---- inspection calls used by tests and benchmarks ------------------------------ */
+
+/* z = M^{-1} r for one vector (host or device pointers, n entries each); which = 0:
+ * the full two-level operator, 1: the local sum only, 2: the coarse term only. */
+ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int which);
+
+/* w = A^T (A p) for one vector (host or device pointers, n entries each). */
+ls_status ls_apply_normal(ls_handle* h, const double* p, double* w);
+
+typedef enum {
+    LS_Q_SIZES = 0,    /* int64[N*4]: n_i, n_I,i, |Xi_i|, k_i per subdomain          */
+    LS_Q_OMEGA = 1,    /* int32[n_i]: Omega_i of subdomain i in [Omega_I, Omega_Gamma] order */
+    LS_Q_XI = 2,       /* int32[|Xi_i|]: Xi_i of subdomain i, ascending             */
+    LS_Q_EIGVALS = 3,  /* float64[k_want]: the computed top eigenvalues of subdomain i,
+                          descending (k_want = min(nev_max + 1, n_i))               */
+    LS_Q_ZBAR = 4,     /* float64[k_i * n_I,i]: coarse basis of subdomain i, one
+                          vector after another, over Omega_I,i ascending            */
+    LS_Q_EIGSTEPS = 5  /* int32[N]: Lanczos steps per subdomain                     */
+} ls_query_kind;
+
+/* Copy one inspected array to the host buffer out (capacity cap elements of the
+ * kind's type).  Returns LS_ERR_INVALID if i is out of range or cap is too small. */
+ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap);
+
+/* Host-only construction of the index sets of Section 3 (no GPU needed).
+ *   Outputs (caller-allocated, sizes from a first call with NULL outputs):
+ *   omega_off[N+1], omega[sum n_i]   Omega_i in [Omega_I, Omega_Gamma] order
+ *   n_interior[N]                    n_I,i
+ *   xi_off[N+1], xi[sum |Xi_i|]      Xi_i ascending
+ * Call with omega == NULL to receive the totals in *omega_total and *xi_total. */
+ls_status ls_build_index_sets(int64_t m, int64_t n, const int64_t* row_ptr,
+                              const int32_t* col, int32_t nparts, const int32_t* part,
+                              int64_t* omega_total, int64_t* xi_total, int64_t* omega_off,
+                              int32_t* omega, int32_t* n_interior, int64_t* xi_off,
+                              int32_t* xi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_SCHWARZ_H */

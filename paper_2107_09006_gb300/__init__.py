@@ -1,0 +1,184 @@
+"""Python binding of libls_schwarz.so: two-level Schwarz PCG for sparse least squares.
+
+The functions below carry the C ABI's names (include/ls_schwarz.h) and only marshal
+arguments: torch tensors and numpy arrays become raw pointers, status codes become
+exceptions.  Every computation runs in the CUDA library; importing this package
+fails loudly if the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libls_schwarz.so")
+
+LS_OK, LS_ERR_INVALID, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_FACTOR, LS_ERR_EIGEN, LS_ERR_NOT_CONVERGED, \
+    LS_ERR_NONFINITE, LS_ERR_DEVICE_TIMEOUT, LS_ERR_UNSUPPORTED = range(10)
+LS_PREC_F64, LS_PREC_F32, LS_PREC_BF16 = 0, 1, 2
+LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS = range(6)
+_PREC = {"f64": LS_PREC_F64, "f32": LS_PREC_F32, "bf16": LS_PREC_BF16}
+
+
+class ls_options(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("nev_max", ctypes.c_int), ("delta_rel", ctypes.c_double),
+                ("s_rel", ctypes.c_double), ("factor_prec", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
+                ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int)]
+
+
+class ls_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("relres_recursive", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("kappa_lanczos", ctypes.c_double), ("n0", ctypes.c_int),
+                ("kmin", ctypes.c_int), ("kmax", ctypes.c_int), ("tau_used", ctypes.c_double),
+                ("delta", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_eig", ctypes.c_double),
+                ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ls status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "ls_default_options": (None, [ctypes.POINTER(ls_options)]),
+        "ls_setup": (ctypes.c_int, [i64, i64, vp, vp, vp, i32, vp, ctypes.c_int, ctypes.POINTER(ls_options), vp,
+                                    ctypes.POINTER(vp)]),
+        "ls_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, dbl, vp, ctypes.POINTER(ls_info)]),
+        "ls_backward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, dbl, vp, vp, ctypes.POINTER(ls_info)]),
+        "ls_free": (None, [vp]),
+        "ls_last_error": (ctypes.c_char_p, []),
+        "ls_handle_info": (ctypes.c_int, [vp, ctypes.POINTER(ls_info)]),
+        "ls_apply_preconditioner": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "ls_apply_normal": (ctypes.c_int, [vp, vp, vp]),
+        "ls_query": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, i64]),
+        "ls_build_index_sets": (ctypes.c_int, [i64, i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIBRARY_PATH = _LIB_PATH
+EXPORTED = ("ls_default_options", "ls_setup", "ls_solve", "ls_backward", "ls_free", "ls_last_error",
+            "ls_handle_info", "ls_apply_preconditioner", "ls_apply_normal", "ls_query", "ls_build_index_sets")
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a contiguous torch tensor or numpy array (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays passed to the library must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"cannot pass {type(a)} to the library")
+
+
+def _check(status: int):
+    if status != LS_OK:
+        raise LSError(status, _lib.ls_last_error().decode())
+
+
+def ls_default_options(**kw) -> ls_options:
+    o = ls_options()
+    _lib.ls_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "factor_prec" and isinstance(v, str):
+            v = _PREC[v]
+        setattr(o, k, v)
+    return o
+
+
+def ls_setup(m, n, row_ptr, col, val, nparts, part, overlap=1, opt=None, stream=None):
+    """Build the two-level preconditioner; returns the opaque handle (an int)."""
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else ls_default_options()
+    _check(_lib.ls_setup(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), int(nparts), _ptr(part),
+                         int(overlap), ctypes.byref(o), stream, ctypes.byref(h)))
+    return h.value
+
+
+def ls_solve(h, b, nrhs, rtol, x, raise_on_fail=True) -> dict:
+    info = ls_info()
+    st = _lib.ls_solve(h, _ptr(b), int(nrhs), float(rtol), _ptr(x), ctypes.byref(info))
+    if raise_on_fail:
+        _check(st)
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def ls_backward(h, b, x, grad_x, nrhs, rtol, grad_b=None, grad_vals=None) -> dict:
+    info = ls_info()
+    _check(_lib.ls_backward(h, _ptr(b), _ptr(x), _ptr(grad_x), int(nrhs), float(rtol), _ptr(grad_b),
+                            _ptr(grad_vals), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def ls_free(h):
+    _lib.ls_free(h)
+
+
+def ls_last_error() -> str:
+    return _lib.ls_last_error().decode()
+
+
+def ls_handle_info(h) -> dict:
+    info = ls_info()
+    _check(_lib.ls_handle_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def ls_apply_preconditioner(h, r, z, which=0):
+    _check(_lib.ls_apply_preconditioner(h, _ptr(r), _ptr(z), int(which)))
+
+
+def ls_apply_normal(h, p, w):
+    _check(_lib.ls_apply_normal(h, _ptr(p), _ptr(w)))
+
+
+def ls_query(h, kind, i, out):
+    _check(_lib.ls_query(h, int(kind), int(i), _ptr(out), int(out.size if isinstance(out, np.ndarray) else out.numel())))
+    return out
+
+
+def ls_build_index_sets(m, n, row_ptr, col, nparts, part):
+    """Host-only index sets: returns (omega_off, omega, n_interior, xi_off, xi) as numpy arrays."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cc = np.ascontiguousarray(col, dtype=np.int32)
+    pp = np.ascontiguousarray(part, dtype=np.int32)
+    ot, xt = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.ls_build_index_sets(int(m), int(n), _ptr(rp), _ptr(cc), int(nparts), _ptr(pp), ctypes.byref(ot),
+                                    ctypes.byref(xt), None, None, None, None, None))
+    om_off = np.zeros(nparts + 1, np.int64)
+    om = np.zeros(max(ot.value, 1), np.int32)
+    nI = np.zeros(nparts, np.int32)
+    xi_off = np.zeros(nparts + 1, np.int64)
+    xi = np.zeros(max(xt.value, 1), np.int32)
+    _check(_lib.ls_build_index_sets(int(m), int(n), _ptr(rp), _ptr(cc), int(nparts), _ptr(pp), None, None,
+                                    _ptr(om_off), _ptr(om), _ptr(nI), _ptr(xi_off), _ptr(xi)))
+    return om_off, om[: ot.value], nI, xi_off, xi[: xt.value]
+
+
+from .solver import Solver, LSSolve  # noqa: E402,F401

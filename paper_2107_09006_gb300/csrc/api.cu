@@ -1,0 +1,920 @@
+// The C ABI (include/ls_schwarz.h): handle, setup orchestration (Algorithm 1 of
+// arXiv 2107.09006 on the device), the PCG solve loop with optional CUDA-graph
+// replay of each iteration, the adjoint solve and the inspection calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ls_schwarz.h"
+#include "host_sets.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+struct LsError : std::runtime_error {
+  ls_status st;
+  LsError(ls_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      throw LsError(e_ == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA,               \
+                    std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw LsError(LS_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+  }
+  void zero(cudaStream_t st) { CK(cudaMemsetAsync(p, 0, n * sizeof(T), st)); }
+  void upload(const std::vector<T>& v, cudaStream_t st) {
+    alloc(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+  template <class U>
+  void upload_from(const U* src, size_t count, cudaStream_t st) {
+    alloc(count);
+    if (count) CK(cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyDefault, st));
+  }
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+__global__ void k_set_diag(double* A, int64_t ld, int64_t from, int64_t to, double v) {
+  for (int64_t k = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < to; k += (int64_t)gridDim.x * blockDim.x)
+    A[k * ld + k] = v;
+}
+
+int pow2_lanes(double avg) {
+  int v = 1;
+  while (v < 32 && v < avg) v <<= 1;
+  return v;
+}
+
+// Extreme eigenvalues of a symmetric tridiagonal matrix by Sturm bisection.
+double tridiag_extreme(const std::vector<double>& d, const std::vector<double>& e, bool largest) {
+  const int k = (int)d.size();
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < k; ++j) {
+    const double r = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < k ? std::fabs(e[j]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = 1.0;
+    for (int j = 0; j < k; ++j) {
+      const double ee = j > 0 ? e[j - 1] : 0.0;
+      q = d[j] - x - (j > 0 ? ee * ee / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  const int target = largest ? k - 1 : 0;  // index of the wanted eigenvalue
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) > target) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+struct ls_handle {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  ls_options opt{};
+  int64_t m = 0, n = 0, nnz = 0;
+  int N = 0, P = 0, lanes_csr = 8, lanes_csc = 32, prec = 0;
+
+  DevBuf<int64_t> row_ptr, col_ptr;
+  DevBuf<int32_t> col, crow, part;
+  DevBuf<double> val, cval;
+
+  DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
+  DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
+  DevBuf<uint8_t> om_int;
+  DevBuf<double> eqs, L64, idiag64;
+  DevBuf<float> L32, idiag32, tsc;
+  DevBuf<__nv_bfloat16> L16;
+  int max_nb = 0;
+  int64_t total_local = 0, total_blocks = 0, fac_elems = 0;
+
+  bool coarse = false;
+  int64_t n0 = 0, n0p = 0;
+  DevBuf<int32_t> coff;
+  DevBuf<int64_t> zoff;
+  DevBuf<double> Z, Xinv;
+
+  DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
+  DevBuf<double> part_pw, part_rz, part_rzo, part_rr, scal, ahist, bhist, sumout;
+  DevBuf<int> ctr;
+  double* pin = nullptr;  // pinned copy of the scalar slots
+  int hist_cap = 0;
+
+  cudaGraphExec_t gexec = nullptr;
+
+  // host copies for queries
+  std::vector<int64_t> h_om_off, h_xi_off;
+  std::vector<int32_t> h_om_paper, h_xi, h_nI, h_k, h_steps;
+  std::vector<double> h_lam;
+  int kwant_cap = 0;
+  ls_info sinfo{};
+
+  ~ls_handle() {
+    if (dev >= 0) cudaSetDevice(dev);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (pin) cudaFreeHost(pin);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+};
+
+namespace {
+
+lsq::CsrDev csr(const ls_handle* h) { return lsq::CsrDev{h->m, h->n, h->row_ptr.p, h->col.p, h->val.p}; }
+lsq::CscDev csc(const ls_handle* h) { return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p}; }
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw LsError(LS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// z = M^{-1} r (which: 0 both terms, 1 local only, 2 coarse only) with the fused dots
+// r.z (and r_old.z for the flexible recurrence) into the partial arrays.
+void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots, bool flex) {
+  cudaStream_t st = h->st;
+  if (which != 0 && which != 1) throw LsError(LS_ERR_INVALID, "precond: which must be 0 or 1");
+  const bool use_coarse = h->coarse && h->n0 > 0 && which != 1;
+  if (which != 2) {
+    lsq::LocalArgs a{};
+    a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
+    a.blk_off = h->blk_off.p; a.blk_tf = h->blk_tf.p; a.blk_poff = h->blk_poff.p;
+    a.fac = h->prec == LS_PREC_F64 ? (const void*)h->L64.p
+          : h->prec == LS_PREC_F32 ? (const void*)h->L32.p : (const void*)h->L16.p;
+    a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
+    a.idiag = h->prec == LS_PREC_F64 ? (const void*)h->idiag64.p : (const void*)h->idiag32.p;
+    a.r = rin; a.y = h->ybuf.p;
+    a.coarse = use_coarse ? 1 : 0;
+    a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
+    a.Z = h->Z.p; a.r0 = h->r0.p;
+    lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, st);
+  }
+  if (use_coarse) lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
+  lsq::ScatterArgs s{};
+  s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
+  s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p;
+  s.r = rin; s.r_old = flex ? h->r_old.p : nullptr; s.z = zout;
+  s.part_rz = dots ? h->part_rz.p : nullptr; s.part_rzo = flex ? h->part_rzo.p : nullptr; s.P = h->P;
+  s.add_coarse_only = which == 2 ? 1 : 0;
+  lsq::launch_scatter(s, st);
+}
+
+// One PCG iteration: w = A^T (A p), alpha, x, r, z = M^{-1} r, beta, p.
+void iteration(ls_handle* h, bool flex) {
+  cudaStream_t st = h->st;
+  lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, st);
+  lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, h->part_pw.p, h->P, h->lanes_csc, st);
+  lsq::launch_cg_update(h->n, h->P, h->part_pw.p, h->part_rz.p, h->p.p, h->w.p, h->x.p, h->r.p,
+                        flex ? h->r_old.p : nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->ahist.p, h->hist_cap, st);
+  precond(h, h->r.p, h->z.p, 0, true, flex);
+  lsq::launch_p_update(h->n, h->P, h->part_rz.p, flex ? h->part_rzo.p : nullptr, h->part_rr.p, h->scal.p,
+                       h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, st);
+  CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
+}
+
+double dev_sum(ls_handle* h) {
+  lsq::launch_finish_sum(h->part_rr.p, h->P, h->sumout.p, h->st);
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, h->sumout.p, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return v;
+}
+
+// PCG on C x = g.  mode 0: g = A^T b with b in h->bv (true residual A^T (b - A x));
+// mode 1: g given in h->tv (true residual g - A^T A x).  Result in h->x.
+ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  const bool flex = h->prec != LS_PREC_F64;
+  const double t0 = now_s();
+  // r = g, gg = ||g||^2
+  if (mode == 0) {
+    lsq::launch_spmv_csc(csc(h), h->bv.p, h->r.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
+  } else {
+    CK(cudaMemcpyAsync(h->r.p, h->tv.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    lsq::launch_dot(n, h->r.p, h->r.p, h->part_rr.p, h->P, st);
+  }
+  const double gg = dev_sum(h);
+  if (!std::isfinite(gg)) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
+  const double gn = std::sqrt(gg);
+  lsq::launch_fill(n, 0.0, h->x.p, st);
+  CK(cudaMemsetAsync(h->ctr.p, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(h->scal.p, 0, sizeof(double) * lsq::S_NSLOT, st));
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  if (gn == 0.0) {
+    CK(cudaStreamSynchronize(st));
+    inf.t_solve = now_s() - t0;
+    if (info) *info = inf;
+    return LS_OK;
+  }
+  auto restart = [&]() {
+    precond(h, h->r.p, h->z.p, 0, true, false);
+    lsq::launch_p_update(n, h->P, h->part_rz.p, nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->bhist.p,
+                         h->hist_cap, h->z.p, h->p.p, 1, st);
+  };
+  restart();
+  check_launch("initial preconditioner apply");
+  const int fixed = h->opt.fixed_iters;
+  const int maxit = fixed > 0 ? fixed : h->opt.maxit;
+  bool converged = false;
+  int it = 0, restarts = 0;
+  double rr = gg;
+  bool graph_this = h->opt.use_graph != 0;
+  while (it < maxit) {
+    if (graph_this) {
+      if (!h->gexec) {  // built once per handle: the iteration only touches fixed buffers
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        iteration(h, flex);
+        CK(cudaStreamEndCapture(st, &g));
+        cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          h->gexec = nullptr;
+          cudaGetLastError();
+          graph_this = false;
+          continue;
+        }
+      }
+      CK(cudaGraphLaunch(h->gexec, st));
+    } else {
+      iteration(h, flex);
+    }
+    CK(cudaStreamSynchronize(st));
+    check_launch("CG iteration");
+    ++it;
+    rr = h->pin[lsq::S_RR];
+    if (h->pin[lsq::S_FLAG] != 0.0 || !std::isfinite(rr))
+      throw LsError(LS_ERR_NONFINITE, "CG breakdown: non-finite or non-positive p.Cp at iteration " + std::to_string(it));
+    if (fixed > 0) continue;
+    if (std::sqrt(rr) <= rtol * gn) {
+      // true residual
+      if (mode == 0) {
+        lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+        lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
+        lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
+      } else {
+        lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+        lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
+        lsq::launch_axpby(n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
+        lsq::launch_dot(n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
+      }
+      const double tt = dev_sum(h);
+      inf.relres_true = std::sqrt(tt) / gn;
+      if (std::sqrt(tt) <= rtol * gn) { converged = true; break; }
+      CK(cudaMemcpyAsync(h->r.p, h->w.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      ++restarts;
+      restart();
+    }
+  }
+  // final statistics
+  inf.iters = it;
+  inf.restarts = restarts;
+  inf.relres_recursive = std::sqrt(rr) / gn;
+  if (!converged) {
+    if (mode == 0) {
+      lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+      lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
+      lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
+    } else {
+      lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+      lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
+      lsq::launch_axpby(n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
+      lsq::launch_dot(n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
+    }
+    inf.relres_true = std::sqrt(dev_sum(h)) / gn;
+  }
+  inf.kappa_lanczos = 0.0;
+  const int nh = std::min(it, h->hist_cap);
+  if (restarts == 0 && nh > 0) {
+    std::vector<double> al(nh), be(nh);
+    CK(cudaMemcpyAsync(al.data(), h->ahist.p, sizeof(double) * nh, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(be.data(), h->bhist.p, sizeof(double) * nh, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<double> d(nh), e(std::max(nh - 1, 0));
+    for (int j = 0; j < nh; ++j) {
+      d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+      if (j + 1 < nh) e[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
+    }
+    const double lmax = tridiag_extreme(d, e, true), lmin = tridiag_extreme(d, e, false);
+    inf.kappa_lanczos = lmin > 0 ? lmax / lmin : 0.0;
+  }
+  inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
+  inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
+  inf.bad_subdomain = -1; inf.eig_steps_max = h->sinfo.eig_steps_max;
+  inf.t_solve = now_s() - t0;
+  if (info) *info = inf;
+  if (!converged && fixed <= 0)
+    return (g_err = "maximum number of iterations reached, true relative residual " +
+                    std::to_string(inf.relres_true), LS_ERR_NOT_CONVERGED);
+  return LS_OK;
+}
+
+template <class F>
+ls_status guarded(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const LsError& e) {
+    g_err = e.what();
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return LS_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return LS_ERR_CUDA;
+  }
+}
+
+template <class T>
+std::vector<T> to_host(const T* src, size_t count) {
+  std::vector<T> v(count);
+  if (count) {
+    cudaError_t e = cudaMemcpy(v.data(), src, count * sizeof(T), cudaMemcpyDefault);
+    if (e != cudaSuccess) throw LsError(LS_ERR_INVALID, std::string("cannot read input array: ") + cudaGetErrorString(e));
+  }
+  return v;
+}
+
+void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, const double* val_in,
+              const int32_t* part_in) {
+  const double t_begin = now_s();
+  cudaStream_t st = h->st;
+  std::vector<int64_t> hrp = to_host(row_ptr_in, (size_t)h->m + 1);
+  const int64_t nnz = hrp[h->m];
+  if (nnz < 0 || hrp[0] != 0) throw LsError(LS_ERR_INVALID, "row_ptr must start at 0 and end at nnz >= 0");
+  std::vector<int32_t> hcol = to_host(col_in, (size_t)nnz);
+  std::vector<double> hval = to_host(val_in, (size_t)nnz);
+  std::vector<int32_t> hpart = to_host(part_in, (size_t)h->n);
+  for (int64_t e = 0; e < nnz; ++e)
+    if (!std::isfinite(hval[e])) throw LsError(LS_ERR_NONFINITE, "A has a non-finite value at entry " + std::to_string(e));
+  lsq::HostSets hs;
+  std::string err = lsq::build_host_sets(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data(), h->coarse, hs);
+  if (!err.empty()) throw LsError(LS_ERR_INVALID, err);
+  h->nnz = nnz;
+  const int N = h->N;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+  h->P = std::max(1, std::min(4 * sms, 2048));
+  h->lanes_csr = pow2_lanes((double)nnz / (double)h->m);
+  h->lanes_csc = pow2_lanes((double)nnz / (double)h->n);
+
+  // matrix copies
+  h->row_ptr.upload(hrp, st);
+  h->col.upload(hcol, st);
+  h->val.upload(hval, st);
+  h->col_ptr.upload(hs.csc_ptr, st);
+  h->crow.upload(hs.csc_row, st);
+  {
+    std::vector<double> cv(nnz);
+    for (int64_t s = 0; s < nnz; ++s) cv[s] = hval[hs.csc_perm[s]];
+    h->cval.upload(cv, st);
+  }
+  h->part.upload(hpart, st);
+
+  // local plan
+  h->total_local = hs.om_off[N];
+  h->total_blocks = hs.blk_off[N];
+  h->fac_elems = hs.fac_elems;
+  h->max_nb = hs.max_nb;
+  h->om_off.upload(hs.om_off, st);
+  h->om_glob.upload(hs.om_glob, st);
+  h->om_int.upload(hs.om_int, st);
+  h->blk_off.upload(hs.blk_off, st);
+  h->blk_tf.upload(hs.blk_tf, st);
+  {
+    std::vector<int64_t> po(hs.blk_poff);
+    po.push_back(hs.fac_elems);
+    h->blk_poff.upload(po, st);
+  }
+  h->map_ptr.upload(hs.map_ptr, st);
+  h->map_idx.upload(hs.map_idx, st);
+  h->int_off.upload(hs.int_off, st);
+  h->int_loc.upload(hs.int_loc, st);
+  h->jj_of.upload(hs.jj_of, st);
+  h->nI.upload(hs.nI, st);
+  {
+    std::vector<int32_t> ig(hs.int_off[N]);
+    for (int i = 0; i < N; ++i)
+      for (int64_t a = hs.int_off[i]; a < hs.int_off[i + 1]; ++a)
+        ig[a] = hs.om_glob[hs.om_off[i] + hs.int_loc[a]];
+    h->int_glob.upload(ig, st);
+  }
+  DevBuf<int32_t> row_sub;
+  {
+    std::vector<int32_t> rs(h->total_local);
+    for (int i = 0; i < N; ++i)
+      for (int64_t e = hs.om_off[i]; e < hs.om_off[i + 1]; ++e) rs[e] = i;
+    row_sub.upload(rs, st);
+  }
+  h->h_om_off = hs.om_off;
+  h->h_om_paper = hs.om_paper;
+  h->h_xi_off = hs.xi_off;
+  h->h_xi = hs.xi;
+  h->h_nI = hs.nI;
+
+  lsq::BandPlan plan{N, h->om_off.p, h->om_glob.p, h->om_int.p, h->blk_off.p, h->blk_tf.p, h->blk_poff.p, row_sub.p};
+
+  // assemble C_ii and C~_ii (Algorithm 1 steps 6-7), shifts, factors
+  DevBuf<double> Cst, Ctst, Bst;
+  Cst.alloc(h->fac_elems); Cst.zero(st);
+  Ctst.alloc(h->fac_elems); Ctst.zero(st);
+  lsq::launch_assemble(plan, csr(h), csc(h), h->part.p, h->total_local, Cst.p, Ctst.p, st);
+  check_launch("assembly");
+  DevBuf<double> cn2, ctn2, sdev;
+  cn2.alloc(N); ctn2.alloc(N);
+  lsq::launch_norms(plan, Cst.p, Ctst.p, cn2.p, ctn2.p, st);
+  std::vector<double> hcn2(N), hctn2(N);
+  CK(cudaMemcpyAsync(hcn2.data(), cn2.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hctn2.data(), ctn2.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  check_launch("norms");
+  double cf2 = 0.0;
+  for (int i = 0; i < N; ++i) cf2 += hcn2[i];
+  const double delta = h->opt.delta_rel * std::sqrt(cf2);
+  std::vector<double> hs_shift(N);
+  for (int i = 0; i < N; ++i) hs_shift[i] = h->opt.s_rel * std::sqrt(hctn2[i]);
+  sdev.upload(hs_shift, st);
+  h->eqs.alloc(h->total_local);
+  Bst.alloc(h->fac_elems);  // prep always writes B = C~_ii + s I
+  lsq::launch_prep(plan, delta, sdev.p, Cst.p, h->eqs.p, Ctst.p, Bst.p, st);
+  check_launch("prep");
+  DevBuf<double> dinv, Bidiag;
+  DevBuf<int> status;
+  dinv.alloc((size_t)h->total_blocks * 1024);
+  status.alloc(N);
+  h->idiag64.alloc((size_t)h->total_blocks * 32);
+  lsq::launch_band_cholesky(plan, Cst.p, h->idiag64.p, dinv.p, status.p, st);
+  std::vector<int> hst(N);
+  CK(cudaMemcpyAsync(hst.data(), status.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  check_launch("local Cholesky");
+  for (int i = 0; i < N; ++i)
+    if (hst[i]) {
+      h->sinfo.bad_subdomain = i;
+      throw LsError(LS_ERR_FACTOR, "Cholesky of C_ii failed in subdomain " + std::to_string(i) + " at local row " +
+                                       std::to_string(hst[i] - 1));
+    }
+
+  h->sinfo.delta = delta;
+  h->kwant_cap = h->opt.nev_max + 1;
+  h->h_k.assign(N, 0);
+  h->h_steps.assign(N, 0);
+  h->coff.alloc(N + 1);
+  h->zoff.alloc(N + 1);
+  {
+    std::vector<int32_t> zc(N + 1, 0);
+    std::vector<int64_t> zz(N + 1, 0);
+    h->coff.upload(zc, st);
+    h->zoff.upload(zz, st);
+  }
+  h->n0 = 0;
+  if (h->coarse) {
+    const double te0 = now_s();
+    Bidiag.alloc((size_t)h->total_blocks * 32);
+    lsq::launch_band_cholesky(plan, Bst.p, Bidiag.p, dinv.p, status.p, st);
+    CK(cudaMemcpyAsync(hst.data(), status.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    check_launch("Cholesky of C~_ii + s I");
+    for (int i = 0; i < N; ++i)
+      if (hst[i]) {
+        h->sinfo.bad_subdomain = i;
+        throw LsError(LS_ERR_FACTOR, "Cholesky of C~_ii + s I failed in subdomain " + std::to_string(i));
+      }
+    const int kw = h->kwant_cap;
+    int K = std::max(48, 2 * kw + 24);
+    K += K & 1;
+    if (K > 160) throw LsError(LS_ERR_UNSUPPORTED, "nev_max too large for the device eigensolver (max 67)");
+    const int keep = kw + (K - kw) / 2;
+    const int64_t vs = (int64_t)h->max_nb * 32;
+    DevBuf<double> V, V2, H, S, vec, lam;
+    DevBuf<int> nconv, steps, est;
+    V.alloc((size_t)N * K * vs); V2.alloc((size_t)N * K * vs);
+    H.alloc((size_t)N * K * K); S.alloc((size_t)N * K * K);
+    vec.alloc((size_t)N * 2 * vs);
+    lam.alloc((size_t)N * kw); lam.zero(st);
+    nconv.alloc(N); steps.alloc(N); est.alloc(N);
+    lsq::EigArgs ea{};
+    ea.P = plan; ea.Bfac = Bst.p; ea.Bidiag = Bidiag.p; ea.Ct = Ctst.p; ea.delta = delta;
+    ea.kwant_cap = kw; ea.Kmax = K; ea.keep = keep; ea.maxit = h->opt.eig_maxit; ea.tol = h->opt.eig_tol;
+    ea.V = V.p; ea.V2 = V2.p; ea.vstride = vs; ea.H = H.p; ea.S = S.p; ea.vec = vec.p; ea.lam = lam.p;
+    ea.nconv = nconv.p; ea.steps = steps.p; ea.status = est.p;
+    lsq::launch_lanczos(ea, st);
+    h->h_lam.assign((size_t)N * kw, 0.0);
+    CK(cudaMemcpyAsync(h->h_lam.data(), lam.p, sizeof(double) * N * kw, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_steps.data(), steps.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hst.data(), est.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    check_launch("local eigensolves");
+    for (int i = 0; i < N; ++i) {
+      h->sinfo.eig_steps_max = std::max(h->sinfo.eig_steps_max, h->h_steps[i]);
+      if (hst[i]) {
+        h->sinfo.bad_subdomain = i;
+        throw LsError(LS_ERR_EIGEN, "eigensolve of subdomain " + std::to_string(i) + " did not converge in " +
+                                        std::to_string(h->h_steps[i]) + " steps");
+      }
+    }
+    // threshold 1/tau (Lemma 2.4 / eq. (3.6)); tau <= 0: max_i lambda_{i, nev_max+1}
+    double thr;
+    if (h->opt.tau > 0) {
+      thr = 1.0 / h->opt.tau;
+    } else {
+      thr = 0.0;
+      for (int i = 0; i < N; ++i) {
+        const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
+        if (ni > h->opt.nev_max) thr = std::max(thr, h->h_lam[(size_t)i * kw + h->opt.nev_max]);
+      }
+    }
+    h->sinfo.tau_used = thr > 0 ? 1.0 / thr : INFINITY;
+    std::vector<int32_t> hcoff(N + 1, 0);
+    std::vector<int64_t> hzoff(N + 1, 0), hwoff(N + 1, 0);
+    int kmin = 1 << 30, kmax = 0;
+    for (int i = 0; i < N; ++i) {
+      const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
+      const int lim = (int)std::min<int64_t>(std::min<int64_t>(kw, ni), h->opt.nev_max);
+      int k = 0;
+      while (k < lim && h->h_lam[(size_t)i * kw + k] > thr) ++k;
+      h->h_k[i] = k;
+      kmin = std::min(kmin, k); kmax = std::max(kmax, k);
+      hcoff[i + 1] = hcoff[i] + k;
+      hzoff[i + 1] = hzoff[i] + (int64_t)k * hs.nI[i];
+      hwoff[i + 1] = hwoff[i] + (int64_t)k * (hs.xi_off[i + 1] - hs.xi_off[i]);
+    }
+    h->n0 = hcoff[N];
+    h->sinfo.kmin = kmin; h->sinfo.kmax = kmax; h->sinfo.n0 = (int)h->n0;
+    h->coff.upload(hcoff, st);
+    h->zoff.upload(hzoff, st);
+    h->Z.alloc(std::max<int64_t>(hzoff[N], 1));
+    lsq::launch_eigvec(ea, h->coff.p, h->zoff.p, h->int_off.p, h->int_loc.p, h->Z.p, st);
+    check_launch("coarse basis");
+    V.release(); V2.release(); H.release(); S.release(); vec.release();
+    if (h->n0 > 0) {
+      DevBuf<int64_t> woff, xi_off, poff;
+      DevBuf<int32_t> xi, xi_sub, pi, pj, ppi, ppj;
+      DevBuf<double> W;
+      woff.upload(hwoff, st);
+      xi_off.upload(hs.xi_off, st);
+      xi.upload(hs.xi, st);
+      {
+        std::vector<int32_t> xs(hs.xi_off[N]);
+        for (int i = 0; i < N; ++i)
+          for (int64_t a = hs.xi_off[i]; a < hs.xi_off[i + 1]; ++a) xs[a] = i;
+        xi_sub.upload(xs, st);
+      }
+      W.alloc(std::max<int64_t>(hwoff[N], 1));
+      lsq::launch_coarse_w(N, xi_off.p, xi.p, h->coff.p, woff.p, h->zoff.p, h->nI.p, csr(h), h->part.p, h->jj_of.p,
+                           h->Z.p, W.p, hs.xi_off[N], xi_sub.p, st);
+      pi.upload(hs.pair_i, st); pj.upload(hs.pair_j, st); poff.upload(hs.pair_off, st);
+      ppi.upload(hs.pair_pi, st); ppj.upload(hs.pair_pj, st);
+      h->n0p = (h->n0 + 31) / 32 * 32;
+      h->Xinv.alloc((size_t)h->n0p * h->n0p);
+      h->Xinv.zero(st);
+      k_set_diag<<<32, 256, 0, st>>>(h->Xinv.p, h->n0p, h->n0, h->n0p, 1.0);
+      lsq::launch_coarse_pairs((int)hs.pair_i.size(), pi.p, pj.p, poff.p, ppi.p, ppj.p, h->coff.p, woff.p, h->zoff.p,
+                               h->nI.p, W.p, h->Z.p, delta, h->n0p, h->Xinv.p, st);
+      check_launch("coarse operator");
+      W.release();
+      DevBuf<double> Y, dinvc;
+      Y.alloc((size_t)h->n0p * h->n0p);
+      dinvc.alloc((size_t)(h->n0p / 32) * 1024);
+      CK(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+      lsq::dense_spd_inverse(h->n0p, h->Xinv.p, Y.p, dinvc.p, status.p, st);
+      int cst = 0;
+      CK(cudaMemcpyAsync(&cst, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      check_launch("coarse factorization");
+      if (cst) throw LsError(LS_ERR_FACTOR, "Cholesky of C_00 failed at row " + std::to_string(cst - 1));
+    }
+    h->sinfo.t_eig = now_s() - te0;
+  } else {
+    h->sinfo.tau_used = 0.0;
+  }
+  Bst.release(); Ctst.release(); Bidiag.release();
+
+  // factor precision of the solve
+  h->prec = h->opt.factor_prec;
+  if (h->prec == LS_PREC_F64) {
+    h->L64.p = Cst.p; h->L64.n = Cst.n; Cst.p = nullptr; Cst.n = 0;
+  } else {
+    h->idiag32.alloc((size_t)h->total_blocks * 32);
+    lsq::launch_convert_f32(h->total_blocks * 32, h->idiag64.p, h->idiag32.p, st);
+    if (h->prec == LS_PREC_F32) {
+      h->L32.alloc(h->fac_elems);
+      lsq::launch_convert_f32(h->fac_elems, Cst.p, h->L32.p, st);
+    } else {
+      h->L16.alloc(h->fac_elems);
+      h->tsc.alloc(std::max<int64_t>(h->fac_elems / 1024, 1));
+      lsq::launch_convert_bf16(h->total_blocks, h->blk_poff.p, Cst.p, h->L16.p, h->tsc.p, st);
+    }
+    CK(cudaStreamSynchronize(st));
+    Cst.release();
+    h->idiag64.release();
+  }
+  // work vectors
+  const int64_t mm = std::max(h->m, h->n);
+  h->x.alloc(h->n); h->r.alloc(h->n); h->r_old.alloc(h->n); h->z.alloc(h->n); h->p.alloc(h->n);
+  h->q.alloc(mm); h->w.alloc(h->n); h->ybuf.alloc(h->total_local);
+  h->r0.alloc(std::max<int64_t>(h->n0p, 1)); h->r0.zero(st);
+  h->y0.alloc(std::max<int64_t>(h->n0p, 1)); h->y0.zero(st);
+  h->tv.alloc(h->n); h->bv.alloc(h->m);
+  h->part_pw.alloc(h->P); h->part_rz.alloc(h->P); h->part_rzo.alloc(h->P); h->part_rr.alloc(h->P);
+  h->scal.alloc(lsq::S_NSLOT); h->sumout.alloc(1);
+  h->hist_cap = std::max(h->opt.maxit, h->opt.fixed_iters) + 8;
+  h->ahist.alloc(h->hist_cap); h->bhist.alloc(h->hist_cap);
+  h->ctr.alloc(1);
+  CK(cudaHostAlloc((void**)&h->pin, sizeof(double) * lsq::S_NSLOT, cudaHostAllocDefault));
+  std::memset(h->pin, 0, sizeof(double) * lsq::S_NSLOT);
+  CK(cudaStreamSynchronize(st));
+  h->sinfo.t_setup = now_s() - t_begin;
+  h->sinfo.bad_subdomain = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ls_default_options(ls_options* o) {
+  if (!o) return;
+  o->tau = 0.0;
+  o->nev_max = 16;
+  o->delta_rel = 1e-10;
+  o->s_rel = 1e-8;
+  o->factor_prec = LS_PREC_F64;
+  o->maxit = 1000;
+  o->coarse = 1;
+  o->fixed_iters = 0;
+  o->eig_maxit = 3000;
+  o->eig_tol = 1e-11;
+  o->use_graph = 1;
+}
+
+const char* ls_last_error(void) { return g_err.c_str(); }
+
+ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   int32_t nparts, const int32_t* part, int overlap, const ls_options* opt, void* stream,
+                   ls_handle** out) {
+  if (out) *out = nullptr;
+  return guarded([&]() -> ls_status {
+    if (!out || !row_ptr || !part || (!col && m > 0) || (!val && m > 0))
+      throw LsError(LS_ERR_INVALID, "null pointer argument");
+    if (m < 1 || n < 1 || m < n) throw LsError(LS_ERR_INVALID, "need m >= n >= 1");
+    if (nparts < 1 || nparts > n) throw LsError(LS_ERR_INVALID, "nparts must lie in [1, n]");
+    if (overlap != 1) throw LsError(LS_ERR_UNSUPPORTED, "only overlap = 1 is defined for the splitting");
+    std::unique_ptr<ls_handle> h(new ls_handle());
+    ls_default_options(&h->opt);
+    if (opt) h->opt = *opt;
+    if (h->opt.factor_prec < 0 || h->opt.factor_prec > 2) throw LsError(LS_ERR_INVALID, "bad factor_prec");
+    if (h->opt.maxit < 1 && h->opt.fixed_iters < 1) throw LsError(LS_ERR_INVALID, "maxit must be positive");
+    if (h->opt.nev_max < 0) throw LsError(LS_ERR_INVALID, "nev_max must be >= 0");
+    if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
+    CK(cudaGetDevice(&h->dev));
+    if (stream) {
+      h->st = (cudaStream_t)stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+      h->own_stream = true;
+    }
+    h->m = m; h->n = n; h->N = nparts;
+    h->coarse = h->opt.coarse != 0 && h->opt.nev_max > 0;
+    h->sinfo.bad_subdomain = -1;
+    try {
+      do_setup(h.get(), row_ptr, col, val, part);
+    } catch (...) {
+      cudaStreamSynchronize(h->st);
+      throw;
+    }
+    *out = h.release();
+    return LS_OK;
+  });
+}
+
+ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x, ls_info* info) {
+  return guarded([&]() -> ls_status {
+    if (!h || !b || !x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
+    if (!(rtol > 0) && h->opt.fixed_iters <= 0) throw LsError(LS_ERR_INVALID, "rtol must be positive");
+    CK(cudaSetDevice(h->dev));
+    ls_status last = LS_OK;
+    for (int k = 0; k < nrhs; ++k) {
+      CK(cudaMemcpyAsync(h->bv.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, h->st));
+      ls_status s = solve_core(h, 0, rtol, info);
+      CK(cudaMemcpyAsync(x + (int64_t)k * h->n, h->x.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      if (s != LS_OK) last = s;
+    }
+    return last;
+  });
+}
+
+ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x, int nrhs, double rtol,
+                      double* grad_b, double* grad_vals, ls_info* info) {
+  return guarded([&]() -> ls_status {
+    if (!h || !b || !x || !grad_x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
+    CK(cudaSetDevice(h->dev));
+    cudaStream_t st = h->st;
+    ls_status last = LS_OK;
+    DevBuf<double> xk, lam, mu;
+    xk.alloc(h->n); lam.alloc(h->n); mu.alloc(h->m);
+    for (int k = 0; k < nrhs; ++k) {
+      CK(cudaMemcpyAsync(h->tv.p, grad_x + (int64_t)k * h->n, sizeof(double) * h->n, cudaMemcpyDefault, st));
+      ls_status s = solve_core(h, 1, rtol, info);
+      if (s != LS_OK) last = s;
+      CK(cudaMemcpyAsync(lam.p, h->x.p, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+      lsq::launch_spmv_csr(csr(h), lam.p, mu.p, h->lanes_csr, st);  // mu = A lambda = grad_b
+      if (grad_b)
+        CK(cudaMemcpyAsync(grad_b + (int64_t)k * h->m, mu.p, sizeof(double) * h->m, cudaMemcpyDefault, st));
+      if (grad_vals) {
+        CK(cudaMemcpyAsync(xk.p, x + (int64_t)k * h->n, sizeof(double) * h->n, cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(h->bv.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, st));
+        lsq::launch_spmv_csr(csr(h), xk.p, h->q.p, h->lanes_csr, st);
+        lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);  // rho = b - A x
+        DevBuf<double> gv;
+        double* gdst = grad_vals;
+        cudaPointerAttributes pa{};
+        bool dev_ptr = cudaPointerGetAttributes(&pa, grad_vals) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        if (!dev_ptr) {
+          gv.alloc(h->nnz);
+          if (k > 0) CK(cudaMemcpyAsync(gv.p, grad_vals, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
+          gdst = gv.p;
+        }
+        lsq::launch_grad_vals(csr(h), h->q.p, lam.p, mu.p, xk.p, gdst, k > 0 ? 1 : 0, st);
+        if (!dev_ptr) CK(cudaMemcpyAsync(grad_vals, gv.p, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+      }
+      check_launch("backward");
+    }
+    CK(cudaStreamSynchronize(st));
+    return last;
+  });
+}
+
+void ls_free(ls_handle* h) { delete h; }
+
+ls_status ls_handle_info(const ls_handle* h, ls_info* info) {
+  if (!h || !info) return LS_ERR_INVALID;
+  *info = h->sinfo;
+  return LS_OK;
+}
+
+ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int which) {
+  return guarded([&]() -> ls_status {
+    if (!h || !r || !z || which < 0 || which > 2) throw LsError(LS_ERR_INVALID, "bad arguments");
+    CK(cudaSetDevice(h->dev));
+    CK(cudaMemcpyAsync(h->tv.p, r, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
+    if (which == 2) {
+      // coarse term alone: run the local kernel for the restriction, then keep only the coarse part
+      precond(h, h->tv.p, h->w.p, 0, false, false);
+      lsq::ScatterArgs s{};
+      s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+      s.coarse = (h->coarse && h->n0 > 0) ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
+      s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p; s.r = h->tv.p; s.z = h->w.p; s.P = h->P;
+      s.add_coarse_only = 1;
+      lsq::launch_scatter(s, h->st);
+    } else {
+      precond(h, h->tv.p, h->w.p, which, false, false);
+    }
+    CK(cudaMemcpyAsync(z, h->w.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    check_launch("preconditioner");
+    return LS_OK;
+  });
+}
+
+ls_status ls_apply_normal(ls_handle* h, const double* p, double* w) {
+  return guarded([&]() -> ls_status {
+    if (!h || !p || !w) throw LsError(LS_ERR_INVALID, "bad arguments");
+    CK(cudaSetDevice(h->dev));
+    CK(cudaMemcpyAsync(h->tv.p, p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
+    lsq::launch_spmv_csr(csr(h), h->tv.p, h->q.p, h->lanes_csr, h->st);
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, h->st);
+    CK(cudaMemcpyAsync(w, h->w.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    check_launch("normal-equations product");
+    return LS_OK;
+  });
+}
+
+ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap) {
+  return guarded([&]() -> ls_status {
+    if (!h || !out) throw LsError(LS_ERR_INVALID, "null argument");
+    const int N = h->N;
+    auto need = [&](int64_t k) {
+      if (cap < k) throw LsError(LS_ERR_INVALID, "output capacity too small: need " + std::to_string(k));
+    };
+    if (kind == LS_Q_SIZES) {
+      need((int64_t)N * 4);
+      int64_t* o = (int64_t*)out;
+      for (int s = 0; s < N; ++s) {
+        o[4 * s + 0] = h->h_om_off[s + 1] - h->h_om_off[s];
+        o[4 * s + 1] = h->h_nI[s];
+        o[4 * s + 2] = h->h_xi_off[s + 1] - h->h_xi_off[s];
+        o[4 * s + 3] = h->h_k.empty() ? 0 : h->h_k[s];
+      }
+      return LS_OK;
+    }
+    if (kind == LS_Q_EIGSTEPS) {
+      need(N);
+      for (int s = 0; s < N; ++s) ((int32_t*)out)[s] = h->h_steps.empty() ? 0 : h->h_steps[s];
+      return LS_OK;
+    }
+    if (i < 0 || i >= N) throw LsError(LS_ERR_INVALID, "subdomain index out of range");
+    if (kind == LS_Q_OMEGA) {
+      const int64_t k = h->h_om_off[i + 1] - h->h_om_off[i];
+      need(k);
+      std::memcpy(out, h->h_om_paper.data() + h->h_om_off[i], sizeof(int32_t) * k);
+    } else if (kind == LS_Q_XI) {
+      const int64_t k = h->h_xi_off[i + 1] - h->h_xi_off[i];
+      need(k);
+      std::memcpy(out, h->h_xi.data() + h->h_xi_off[i], sizeof(int32_t) * k);
+    } else if (kind == LS_Q_EIGVALS) {
+      if (h->h_lam.empty()) throw LsError(LS_ERR_INVALID, "no eigensolve was run");
+      const int64_t ni = h->h_om_off[i + 1] - h->h_om_off[i];
+      const int64_t k = std::min<int64_t>(h->kwant_cap, ni);
+      need(k);
+      std::memcpy(out, h->h_lam.data() + (size_t)i * h->kwant_cap, sizeof(double) * k);
+    } else if (kind == LS_Q_ZBAR) {
+      const int64_t k = (int64_t)h->h_k[i] * h->h_nI[i];
+      need(k);
+      if (k) {
+        int64_t off = 0;
+        for (int s = 0; s < i; ++s) off += (int64_t)h->h_k[s] * h->h_nI[s];
+        CK(cudaSetDevice(h->dev));
+        CK(cudaMemcpy(out, h->Z.p + off, sizeof(double) * k, cudaMemcpyDeviceToHost));
+      }
+    } else {
+      throw LsError(LS_ERR_INVALID, "unknown query kind");
+    }
+    return LS_OK;
+  });
+}
+
+ls_status ls_build_index_sets(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t nparts,
+                              const int32_t* part, int64_t* omega_total, int64_t* xi_total, int64_t* omega_off,
+                              int32_t* omega, int32_t* n_interior, int64_t* xi_off, int32_t* xi) {
+  return guarded([&]() -> ls_status {
+    if (!row_ptr || !col || !part) throw LsError(LS_ERR_INVALID, "null pointer argument");
+    lsq::HostSets hs;
+    std::string err = lsq::build_host_sets(m, n, row_ptr, col, nparts, part, false, hs);
+    if (!err.empty()) throw LsError(LS_ERR_INVALID, err);
+    if (omega_total) *omega_total = hs.om_off[nparts];
+    if (xi_total) *xi_total = hs.xi_off[nparts];
+    if (omega) {
+      std::memcpy(omega, hs.om_paper.data(), sizeof(int32_t) * hs.om_paper.size());
+      std::memcpy(omega_off, hs.om_off.data(), sizeof(int64_t) * hs.om_off.size());
+      std::memcpy(n_interior, hs.nI.data(), sizeof(int32_t) * hs.nI.size());
+      std::memcpy(xi_off, hs.xi_off.data(), sizeof(int64_t) * hs.xi_off.size());
+      std::memcpy(xi, hs.xi.data(), sizeof(int32_t) * hs.xi.size());
+    }
+    return LS_OK;
+  });
+}
+
+}  // extern "C"

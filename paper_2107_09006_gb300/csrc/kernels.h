@@ -1,0 +1,122 @@
+// Launchers of the device kernels (host-callable; all asynchronous on `st`).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lsq {
+
+// ---- sparse products and CG vector kernels (k_krylov.cu) ----------------------------
+struct CsrDev { int64_t m, n; const int64_t* row_ptr; const int32_t* col; const double* val; };
+struct CscDev { int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val; };
+
+// Scalar slots of the CG state kept on the device.
+enum { S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_NSLOT = 8 };
+
+void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, cudaStream_t st);
+// w = A^T q; if part != nullptr also writes per-block partial sums of d.w (d = w if d == nullptr).
+void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, double* part,
+                     int P, int lanes, cudaStream_t st);
+void launch_cg_update(int64_t n, int P, const double* part_pw, const double* part_rz, const double* p,
+                      const double* w, double* x, double* r, double* r_old, double* part_rr,
+                      double* scal, int* ctr, double* alpha_hist, int hist_cap, cudaStream_t st);
+void launch_p_update(int64_t n, int P, const double* part_rz, const double* part_rzo,
+                     const double* part_rr, double* scal, int* ctr, double* beta_hist, int hist_cap,
+                     const double* z, double* p, int init, cudaStream_t st);
+void launch_dot(int64_t n, const double* a, const double* b, double* part, int P, cudaStream_t st);
+void launch_finish_sum(const double* part, int P, double* out, cudaStream_t st);
+void launch_axpby(int64_t n, double alpha, const double* a, double beta, const double* b, double* out,
+                  cudaStream_t st);
+void launch_fill(int64_t n, double v, double* out, cudaStream_t st);
+
+struct ScatterArgs {
+  int64_t n;
+  const int64_t* map_ptr; const int64_t* map_idx; const double* y;  // local solutions
+  // coarse prolongation (coarse == 0: skipped)
+  int coarse; const int32_t* part; const int32_t* jj_of; const int64_t* zoff; const int32_t* coff;
+  const int32_t* nI; const double* Z; const double* y0;
+  const double* r; const double* r_old;  // for the fused dots (r_old may be null)
+  double* z; double* part_rz; double* part_rzo; int P;
+  int add_coarse_only;  // 1: z = coarse term only; 2: z = local sum only
+};
+void launch_scatter(const ScatterArgs& a, cudaStream_t st);
+void launch_gemv(int64_t n0, const double* X, const double* r0, double* y0, cudaStream_t st);
+void launch_grad_vals(const CsrDev& A, const double* rho, const double* lam, const double* mu,
+                      const double* x, double* g, int accumulate, cudaStream_t st);
+
+// ---- block-envelope matrices (k_band.cu) -------------------------------------------
+struct BandPlan {
+  int N;
+  const int64_t* om_off; const int32_t* om_glob; const uint8_t* om_int;
+  const int64_t* blk_off; const int32_t* blk_tf; const int64_t* blk_poff;
+  const int32_t* row_sub;  // subdomain of each local position (sum n_i entries)
+};
+// Assemble C_ii (all rows of A touching Omega_i) and C~_ii (rows Xi_i) into two
+// zeroed storages (lower triangles).
+void launch_assemble(const BandPlan& P, const CsrDev& A, const CscDev& At, const int32_t* part,
+                     int64_t total_local, double* Cst, double* Ctst, cudaStream_t st);
+// Per subdomain: cn2[i] = sum over interior rows of C of squared row norms (so that
+// sum_i cn2[i] = ||C||_F^2); ctn2[i] = ||C~_ii||_F^2.
+void launch_norms(const BandPlan& P, const double* Cst, const double* Ctst, double* cn2,
+                  double* ctn2, cudaStream_t st);
+// C_ii += delta I, equilibrate C_ii with eqs = diag(C_ii)^{-1/2}; B_i = C~_ii + s_i I.
+void launch_prep(const BandPlan& P, double delta, const double* s, double* Cst, double* eqs,
+                 const double* Ctst, double* Bst, cudaStream_t st);
+// In-place Cholesky of every subdomain's matrix; idiag = 1 / diag(L);
+// status[i] = 0 or 1 + the local row of the first nonpositive pivot.
+// dinv: scratch of 1024 doubles per block row (inverse diagonal tiles).
+void launch_band_cholesky(const BandPlan& P, double* st_fac, double* idiag, double* dinv, int* status,
+                          cudaStream_t st);
+void launch_convert_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
+// One CTA per block row; poff has (number of block rows + 1) entries.
+void launch_convert_bf16(int64_t nblocks, const int64_t* poff, const double* src, __nv_bfloat16* dst,
+                         float* tsc, cudaStream_t st);
+
+struct LocalArgs {
+  const int64_t* om_off; const int32_t* om_glob; const double* eqs;
+  const int64_t* blk_off; const int32_t* blk_tf; const int64_t* blk_poff;
+  const void* fac; const float* tsc; const void* idiag;  // idiag: double (F64) or float
+  const double* r; double* y;
+  int coarse; const int64_t* int_off; const int32_t* int_glob; const int64_t* zoff;
+  const int32_t* coff; const double* Z; double* r0;
+};
+size_t local_solve_smem(int prec, int max_nb);
+void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
+
+// ---- eigen setup (k_lanczos.cu) ----------------------------------------------------
+struct EigArgs {
+  BandPlan P;
+  const double* Bfac; const double* Bidiag;  // chol(C~_ii + s I)
+  const double* Ct;                          // C~_ii (lower), for D C_ii D products
+  double delta;                              // D C_ii D = D C~_ii D + delta D
+  int kwant_cap;                             // nev_max + 1
+  int Kmax; int keep;                        // basis size and restart size
+  int maxit; double tol;
+  double* V; double* V2; int64_t vstride;    // per subdomain: Kmax vectors of vstride
+  double* H; double* S;                      // per subdomain Kmax*Kmax
+  double* vec;                               // per subdomain 3 * vstride work vectors
+  double* lam;                               // per subdomain kwant_cap eigenvalues (out)
+  int* nconv; int* steps; int* status;
+};
+size_t lanczos_smem(int max_nb);
+void launch_lanczos(const EigArgs& a, cudaStream_t st);
+// Z_i = interior rows of L_B^{-T} U_i for the first k_i Ritz vectors U_i (V holds them).
+void launch_eigvec(const EigArgs& a, const int32_t* coff, const int64_t* zoff,
+                   const int64_t* int_off, const int32_t* int_loc, double* Z, cudaStream_t st);
+
+// ---- coarse operator (k_coarse.cu) -------------------------------------------------
+void launch_coarse_w(int N, const int64_t* xi_off, const int32_t* xi, const int32_t* coff,
+                     const int64_t* woff, const int64_t* zoff, const int32_t* nI, const CsrDev& A,
+                     const int32_t* part, const int32_t* jj_of, const double* Z, double* W,
+                     int64_t total_xi, const int32_t* xi_sub, cudaStream_t st);
+void launch_coarse_pairs(int npairs, const int32_t* pi, const int32_t* pj, const int64_t* poff,
+                         const int32_t* ppi, const int32_t* ppj, const int32_t* coff,
+                         const int64_t* woff, const int64_t* zoff, const int32_t* nI,
+                         const double* W, const double* Z, double delta, int64_t n0, double* C00,
+                         cudaStream_t st);
+// Dense SPD inverse through its Cholesky factor (tiles of 32; n a multiple of 32,
+// row-major, full storage): A is replaced by A^{-1}; Y (n x n) and dinv (n/32 * 1024)
+// are scratch; *status (device) receives 0 or 1 + the first failing row.
+void dense_spd_inverse(int64_t n, double* A, double* Y, double* dinv, int* status, cudaStream_t st);
+
+}  // namespace lsq

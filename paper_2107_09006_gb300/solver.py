@@ -1,0 +1,130 @@
+"""Object wrapper around the C ABI and the autograd function whose backward is the
+adjoint solve.  PyTorch only provides device memory here; all arithmetic runs in
+libls_schwarz.so."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (ls_setup, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info,
+               ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI,
+               LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS)
+
+
+def _dev(a, dtype, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+
+
+class Solver:
+    """Owns one ls_handle: ``Solver(m, n, row_ptr, col, val, part, nparts, **options)``.
+
+    Options are the fields of ls_options (tau, nev_max, delta_rel, s_rel, factor_prec
+    ('f64' | 'f32' | 'bf16'), maxit, coarse, fixed_iters, eig_maxit, eig_tol,
+    use_graph).  Arrays may be numpy arrays or tensors; they are copied by setup.
+    """
+
+    def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", **options):
+        self.device = torch.device(device)
+        self.m, self.n = int(m), int(n)
+        self.row_ptr = _dev(row_ptr, torch.int64, self.device)
+        self.col = _dev(col, torch.int32, self.device)
+        self.val = _dev(val, torch.float64, self.device)
+        self.part = _dev(part, torch.int32, self.device)
+        self.nparts = int(nparts)
+        self.opt = ls_default_options(**options)
+        with torch.cuda.device(self.device):
+            self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1, self.opt)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ls_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return ls_handle_info(self.h)
+
+    def solve(self, b, rtol=1e-8, raise_on_fail=True):
+        """x = argmin ||A x - b|| for b of shape [m] or [nrhs, m] (one right-hand side per row)."""
+        b = _dev(b, torch.float64, self.device)
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        x = torch.empty((self.n,) if b.dim() == 1 else (nrhs, self.n), dtype=torch.float64, device=self.device)
+        info = ls_solve(self.h, b, nrhs, rtol, x, raise_on_fail)
+        return x, info
+
+    def backward(self, b, x, grad_x, rtol=1e-10, want_b=True, want_vals=True):
+        b = _dev(b, torch.float64, self.device)
+        x = _dev(x, torch.float64, self.device)
+        g = _dev(grad_x, torch.float64, self.device)
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        gb = torch.empty_like(b) if want_b else None
+        gv = torch.empty(self.val.shape[0], dtype=torch.float64, device=self.device) if want_vals else None
+        info = ls_backward(self.h, b, x, g, nrhs, rtol, gb, gv)
+        return gb, gv, info
+
+    def apply_preconditioner(self, r, which=0):
+        r = _dev(r, torch.float64, self.device)
+        z = torch.empty_like(r)
+        ls_apply_preconditioner(self.h, r, z, which)
+        return z
+
+    def apply_normal(self, p):
+        p = _dev(p, torch.float64, self.device)
+        w = torch.empty_like(p)
+        ls_apply_normal(self.h, p, w)
+        return w
+
+    # ---- inspection -------------------------------------------------------------
+    def sizes(self) -> np.ndarray:
+        out = np.zeros(self.nparts * 4, np.int64)
+        return ls_query(self.h, LS_Q_SIZES, 0, out).reshape(self.nparts, 4)
+
+    def omega(self, i) -> np.ndarray:
+        return ls_query(self.h, LS_Q_OMEGA, i, np.zeros(int(self.sizes()[i, 0]), np.int32))
+
+    def xi(self, i) -> np.ndarray:
+        return ls_query(self.h, LS_Q_XI, i, np.zeros(int(self.sizes()[i, 2]), np.int32))
+
+    def eigvals(self, i) -> np.ndarray:
+        ni = int(self.sizes()[i, 0])
+        return ls_query(self.h, LS_Q_EIGVALS, i, np.zeros(min(self.opt.nev_max + 1, ni), np.float64))
+
+    def zbar(self, i) -> np.ndarray:
+        s = self.sizes()[i]
+        k, nI = int(s[3]), int(s[1])
+        out = np.zeros(max(k * nI, 1), np.float64)
+        if k:
+            ls_query(self.h, LS_Q_ZBAR, i, out)
+        return out[: k * nI].reshape(k, nI)
+
+    def eig_steps(self) -> np.ndarray:
+        return ls_query(self.h, LS_Q_EIGSTEPS, 0, np.zeros(self.nparts, np.int32))
+
+
+class LSSolve(torch.autograd.Function):
+    """x = LSSolve.apply(vals, b, solver, rtol): the LS solution for A with the solver's
+    pattern and values ``vals``.  Backward is the adjoint solve lambda = C^{-1} grad_x
+    with the same preconditioner: grad_b = A lambda, grad_vals = rho lambda^T - (A lambda) x^T
+    on the stored entries (rho = b - A x).  The preconditioner is built from the
+    solver's own values; ``vals`` must equal them (the solver is rebuilt by the caller
+    when A changes)."""
+
+    @staticmethod
+    def forward(ctx, vals, b, solver, rtol=1e-10):
+        x, info = solver.solve(b.detach(), rtol)
+        ctx.solver, ctx.rtol = solver, rtol
+        ctx.save_for_backward(b.detach(), x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        b, x = ctx.saved_tensors
+        gb, gv, _ = ctx.solver.backward(b, x, gx.contiguous(), ctx.rtol)
+        return gv, gb, None, None
