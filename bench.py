@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: seconds to solve the n = 1,048,576 sparse least-squares problem to a true
+normal-equations relative residual of 1e-8 with two-level Schwarz PCG on one GB300.
+
+Workload (synthetic, seed 0): 1024 x 1024 grid of unknowns, m = 4n random rows with 8
+nonzeros inside Chebyshev radius 3 of a random centre (N(0,1) values) plus 1e-2 I rows;
+256 subdomains of 64 x 64 columns, overlap 1, at most 32 coarse vectors each (tau
+automatic).  A step is one complete ls_solve (x_0 = 0 to ||A^T(b - Ax)|| <= 1e-8 ||A^T b||);
+setup is timed separately.  The headline form is the mixed one (FP32 local factors
+inside an FP64 flexible CG); the plain FP64 form runs on the same problem beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU: replicas only (every rank solves its own copy; max time over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "n=1M LS solve s to 1e-8 normal-eq rel resid, mixed vs FP64 form; apply HBM GB/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16"], help="headline form")
+    ap.add_argument("--forms", default="f32,f64", help="forms to run (comma list)")
+    ap.add_argument("--side", type=int, default=1024)
+    ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--nev", type=int, default=32)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--sample-side", type=int, default=256, help="grid side of the CPU-oracle sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy, burst)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def local_solve_bytes(st: dict, form: str) -> int:
+    """Algorithmic bytes of one local-solve launch: the stored factor tiles read by the
+    forward and the backward sweep, the inverse diagonal, the gather of r and the
+    write of y (index, r value, scale, y per local entry), the coarse restriction
+    (Zbar once plus r at the interior columns)."""
+    es = {"f64": 8, "f32": 4, "bf16": 2}[form]
+    fac = 2 * st["fac_elems"] * es
+    if form == "bf16":
+        fac += 2 * (st["fac_elems"] // 1024) * 4
+    idiag = 2 * st["total_blocks"] * 32 * (8 if form == "f64" else 4)
+    gather = st["total_local"] * (4 + 8 + 8 + 8)
+    coarse = st["zbar_elems"] * 8
+    return fac + idiag + gather + coarse
+
+
+def spmv_bytes(m: int, n: int, nnz: int) -> int:
+    """Algorithmic bytes of q = A p then w = A^T q with the fused p.w: both index/value
+    streams, both pointer arrays, the vectors read once and the results written once."""
+    csr = nnz * 12 + (m + 1) * 8 + n * 8 + m * 8
+    csc = nnz * 12 + (n + 1) * 8 + m * 8 + n * 8 + n * 8
+    return csr + csc
+
+
+def cpu_oracle_sample(side: int, block: int, nev: int, rtol: float, reps: int = 1) -> dict:
+    """Runs the FP64 oracle (banded mode) on a side x side sample of the same workload in a
+    single-threaded subprocess: setup once, then `reps` timed solves."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import oracle as O
+from workloads import config_scale
+P = config_scale(side={side}, block={block})
+A = O.schwarz.as_csr(P.m, P.n, P.row_ptr, P.col, P.val)
+t = time.time()
+M = O.build_two_level(A, P.part, P.nparts, tau=0.0, nev_max={nev}, mode="banded")
+ts = time.time() - t
+times, iters = [], 0
+for _ in range({reps}):
+    t = time.time()
+    x, info = O.pcg(A, P.b, M.apply, rtol={rtol})
+    times.append(time.time() - t)
+    iters = info["iters"]
+print(json.dumps(dict(n=P.n, N=P.nparts, setup_s=ts, solve_s=times, iters=iters, n0=M.n0)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_full = args.side * args.side
+    d = cpu_oracle_sample(args.sample_side, args.block, args.nev, args.rtol, reps=args.warmup + args.steps)
+    times = d["solve_s"][args.warmup:]
+    scale = n_full / d["n"]
+    val = statistics.mean(times) * scale
+    sample = (f"oracle (FP64 numpy/scipy, banded LAPACK factors, ARPACK eigensolves) on a "
+              f"{args.sample_side}x{args.sample_side} grid ({d['N']} subdomains of {args.block}x{args.block}, "
+              f"n={d['n']}), {d['iters']} PCG iterations; solve seconds scaled by n ratio {scale:.1f}")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1000, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"grid{args.side}-r3k8-N{(args.side // args.block) ** 2}", "rtol": args.rtol},
+            "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2107_09006_gb300 import Solver, ls_solve
+    from workloads import config_scale
+
+    t = time.time()
+    P = config_scale(side=args.side, block=args.block)
+    log(f"[bench] workload generated in {time.time() - t:.1f}s: m={P.m} n={P.n} nnz={P.nnz} N={P.nparts}")
+    stream = torch.cuda.current_stream(dev)
+    hbm_peak, peak_src = peaks()
+    forms = [f for f in args.forms.split(",") if f]
+    if args.prec not in forms:
+        forms.insert(0, args.prec)
+    b_dev = torch.as_tensor(P.b, device=dev)
+    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    results, clocks, e2e, launches = {}, None, None, 0
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for form in forms:
+        t = time.time()
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000)
+        torch.cuda.synchronize(dev)
+        setup_s = time.time() - t
+        sinfo = S.info()
+        st = S.storage()
+        log(f"[bench] {form}: setup {setup_s:.2f}s (eig {sinfo['t_eig']:.2f}s) n0={sinfo['n0']} "
+            f"k in [{sinfo['kmin']},{sinfo['kmax']}] steps<= {sinfo['eig_steps_max']} fac={st['fac_elems']}")
+        for _ in range(args.warmup):
+            ls_solve(S.h, b_dev, 1, args.rtol, x_dev)
+        headline = form == args.prec
+        ck = None
+        if headline:
+            ck = Clocks(dev.index or 0)
+            ck.start()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [ls_solve(S.h, b_dev, 1, args.rtol, x_dev) for _ in range(args.steps)]
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        if headline:
+            clocks = ck.stop()
+        if world > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        nl = sum(i["local_launches"] for i in infos)
+        ms_local = sum(i["ms_local"] for i in infos) / max(nl, 1)
+        its = sum(i["iters"] for i in infos)
+        ms_spmv = sum(i["ms_spmv"] for i in infos) / max(its, 1)
+        lb = local_solve_bytes(st, form)
+        sb = spmv_bytes(P.m, P.n, P.nnz)
+        loc_gbs = lb / (ms_local * 1e-3) / 1e9
+        spmv_gbs = sb / (ms_spmv * 1e-3) / 1e9
+        results[form] = {
+            "value": ms / 1000.0, "iterations": infos[-1]["iters"], "relres_true": infos[-1]["relres_true"],
+            "setup_s": setup_s, "eig_s": sinfo["t_eig"], "n0": sinfo["n0"], "kappa_lanczos": infos[-1]["kappa_lanczos"],
+            "local_solve": {"ms_per_launch": ms_local, "bytes_per_launch": lb, "GBps": loc_gbs,
+                            "frac": loc_gbs / hbm_peak, "share_of_step": nl * ms_local / (ms * args.steps)},
+            "spmv_pair": {"ms_per_iter": ms_spmv, "bytes_per_iter": sb, "GBps": spmv_gbs, "frac": spmv_gbs / hbm_peak},
+        }
+        if headline:
+            launches = sum(i["launches"] for i in infos)
+            # end to end through the public call with pinned host buffers
+            bh = torch.as_tensor(P.b).pin_memory()
+            xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
+            ls_solve(S.h, bh, 1, args.rtol, xh)
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                ls_solve(S.h, bh, 1, args.rtol, xh)
+            f1.record(stream)
+            barrier()
+            e2e_ms = f0.elapsed_time(f1) / args.steps
+            xerr = float(np.linalg.norm(xh.numpy() - x_dev.cpu().numpy()) / np.linalg.norm(x_dev.cpu().numpy()))
+            e2e = {"value": e2e_ms / 1000.0, "unit": "s", "h2d_bytes_per_step": P.m * 8, "d2h_bytes_per_step": P.n * 8,
+                   "x_vs_device_run": xerr}
+        S.close()
+        del S
+        torch.cuda.empty_cache()
+
+    head = results[args.prec]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["value"] * 1000, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f64": "f64", "bf16": "bf16"}[args.prec], "data": "synthetic",
+        "config": {"workload": f"grid{args.side}-r3k8-N{P.nparts}: n={P.n}, m={P.m}, nnz={P.nnz}, "
+                               f"{P.nparts} subdomains {args.block}x{args.block}, overlap 1, nev_max {args.nev}, tau auto",
+                   "rtol": args.rtol, "form": {"f32": "mixed: FP32 local factors, FP64 flexible CG",
+                                                "f64": "plain FP64", "bf16": "mixed: BF16 local factors"}[args.prec],
+                   "l2": "inputs larger than L2 (factors alone exceed 129 MB)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": head["local_solve"]["GBps"], "peak": hbm_peak, "unit": "GB/s",
+                     "frac": head["local_solve"]["frac"], "traffic": None,
+                     "kernel": "k_local_solve (batched envelope trisolves, one CTA per subdomain)",
+                     "bytes_per_launch": head["local_solve"]["bytes_per_launch"],
+                     "ms_per_launch": head["local_solve"]["ms_per_launch"], "peak_source": peak_src},
+        "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+        "iterations": head["iterations"], "setup_s": head["setup_s"], "forms": results,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            d = cpu_oracle_sample(args.sample_side, args.block, args.nev, args.rtol)
+            scale = P.n / d["n"]
+            line["cpu_baseline"] = {
+                "value": d["solve_s"][0] * scale, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": (f"oracle (FP64 numpy/scipy, single thread) on a {args.sample_side}x{args.sample_side} "
+                           f"grid of the same generator ({d['N']} subdomains {args.block}x{args.block}, n={d['n']}): "
+                           f"{d['iters']} PCG iterations in {d['solve_s'][0]:.2f}s, scaled by n ratio {scale:.1f}; "
+                           f"oracle setup {d['setup_s']:.1f}s not included")}
+        except Exception as ex:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": str(ex)[:300]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -73,6 +73,8 @@ typedef struct {
     int eig_maxit;     /* limit on Lanczos steps per subdomain eigensolve               */
     double eig_tol;    /* relative Ritz residual tolerance of the eigensolve           */
     int use_graph;     /* 1: replay each CG iteration as a captured CUDA graph          */
+    int time_kernels;  /* 1: time the local-solve and sparse-product launches of each
+                          iteration with CUDA events (reported in ls_info)           */
 } ls_options;
 
 typedef struct {
@@ -90,13 +92,18 @@ typedef struct {
     double t_solve;          /* seconds: the last ls_solve / ls_backward                    */
     int bad_subdomain;       /* subdomain of a factor / eigen failure, else -1              */
     int eig_steps_max;       /* most Lanczos steps one subdomain needed                     */
+    double ms_local;         /* with time_kernels: total ms of the local-solve launches     */
+    double ms_spmv;          /* with time_kernels: total ms of the A and A^T launches       */
+    double ms_coarse;        /* with time_kernels: total ms of the coarse GEMV launches      */
+    int local_launches;      /* local-solve launches of the last solve                      */
+    int launches;            /* kernels launched by the last solve (all of this library's)  */
 } ls_info;
 
 typedef struct ls_handle ls_handle;
 
 /* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
- * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1. */
+ * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping
@@ -167,7 +174,10 @@ typedef enum {
                           descending (k_want = min(nev_max + 1, n_i))               */
     LS_Q_ZBAR = 4,     /* float64[k_i * n_I,i]: coarse basis of subdomain i, one
                           vector after another, over Omega_I,i ascending            */
-    LS_Q_EIGSTEPS = 5  /* int32[N]: Lanczos steps per subdomain                     */
+    LS_Q_EIGSTEPS = 5, /* int32[N]: Lanczos steps per subdomain                     */
+    LS_Q_STORAGE = 6   /* int64[8]: factor elements (all subdomains), sum n_i, block
+                          rows, coarse-basis elements, n0, padded n0, nnz(A), factor
+                          precision (ls_precision)                                  */
 } ls_query_kind;
 
 /* Copy one inspected array to the host buffer out (capacity cap elements of the

@@ -17,6 +17,7 @@ import numpy as np
 import scipy.linalg as sl
 import scipy.sparse as sp
 import scipy.sparse.linalg as sla
+from scipy.linalg import lapack as sla_lapack
 
 EPS = np.finfo(np.float64).eps
 
@@ -237,16 +238,16 @@ def _gevp_banded(Cii, Ct, s, bw, interior, kwant):
     d = interior.astype(np.float64)
     DCD = sp.diags(d) @ Cii @ sp.diags(d)
 
-    # L^{-1} x and L^{-T} x with the banded factor (the banded triangular solves of LAPACK)
+    # L^{-1} x and L^{-T} x with the banded factor (LAPACK's triangular banded solve)
     def lsolve(x):
-        return sl.solve_banded((bw, 0), Lb, x)
-
-    Ub = np.zeros_like(Lb)  # upper band of L^T: Ub[bw - d, j + d] = L[j + d, j]
-    for dd in range(bw + 1):
-        Ub[bw - dd, dd:] = Lb[dd, : ni - dd]
+        y, info = sla_lapack.dtbtrs(Lb, x.reshape(-1, 1), uplo='L', trans='N')
+        assert info == 0
+        return y.ravel()
 
     def ltsolve(x):
-        return sl.solve_banded((0, bw), Ub, x)
+        y, info = sla_lapack.dtbtrs(Lb, x.reshape(-1, 1), uplo='L', trans='T')
+        assert info == 0
+        return y.ravel()
 
     def mv(u):
         return lsolve(DCD @ ltsolve(u))

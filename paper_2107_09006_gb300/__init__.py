@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libls_schwarz.so")
 LS_OK, LS_ERR_INVALID, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_FACTOR, LS_ERR_EIGEN, LS_ERR_NOT_CONVERGED, \
     LS_ERR_NONFINITE, LS_ERR_DEVICE_TIMEOUT, LS_ERR_UNSUPPORTED = range(10)
 LS_PREC_F64, LS_PREC_F32, LS_PREC_BF16 = 0, 1, 2
-LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS = range(6)
+LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE = range(7)
 _PREC = {"f64": LS_PREC_F64, "f32": LS_PREC_F32, "bf16": LS_PREC_BF16}
 
 
@@ -26,7 +26,7 @@ class ls_options(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("nev_max", ctypes.c_int), ("delta_rel", ctypes.c_double),
                 ("s_rel", ctypes.c_double), ("factor_prec", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
-                ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int)]
+                ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -34,7 +34,9 @@ class ls_info(ctypes.Structure):
                 ("relres_true", ctypes.c_double), ("kappa_lanczos", ctypes.c_double), ("n0", ctypes.c_int),
                 ("kmin", ctypes.c_int), ("kmax", ctypes.c_int), ("tau_used", ctypes.c_double),
                 ("delta", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_eig", ctypes.c_double),
-                ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int)]
+                ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int),
+                ("ms_local", ctypes.c_double), ("ms_spmv", ctypes.c_double), ("ms_coarse", ctypes.c_double),
+                ("local_launches", ctypes.c_int), ("launches", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

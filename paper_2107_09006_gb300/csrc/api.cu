@@ -148,6 +148,7 @@ struct ls_handle {
   int hist_cap = 0;
 
   cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // kernel timing
 
   // host copies for queries
   std::vector<int64_t> h_om_off, h_xi_off;
@@ -159,6 +160,8 @@ struct ls_handle {
   ~ls_handle() {
     if (dev >= 0) cudaSetDevice(dev);
     if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
     if (pin) cudaFreeHost(pin);
     if (own_stream && st) cudaStreamDestroy(st);
   }
@@ -176,9 +179,10 @@ void check_launch(const char* what) {
 
 // z = M^{-1} r (which: 0 both terms, 1 local only, 2 coarse only) with the fused dots
 // r.z (and r_old.z for the flexible recurrence) into the partial arrays.
-void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots, bool flex) {
+void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots, bool flex, bool timed = false) {
   cudaStream_t st = h->st;
   if (which != 0 && which != 1) throw LsError(LS_ERR_INVALID, "precond: which must be 0 or 1");
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
   const bool use_coarse = h->coarse && h->n0 > 0 && which != 1;
   if (which != 2) {
     lsq::LocalArgs a{};
@@ -194,7 +198,9 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
     a.Z = h->Z.p; a.r0 = h->r0.p;
     lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, st);
   }
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
   if (use_coarse) lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
   s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
@@ -206,13 +212,19 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
 }
 
 // One PCG iteration: w = A^T (A p), alpha, x, r, z = M^{-1} r, beta, p.
+// Kernels one iteration launches (for the launch count reported in ls_info).
+int iteration_launches(const ls_handle* h) { return 6 + ((h->coarse && h->n0 > 0) ? 1 : 0); }
+
 void iteration(ls_handle* h, bool flex) {
   cudaStream_t st = h->st;
+  const bool timed = h->opt.time_kernels != 0;
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
   lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, st);
   lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, h->part_pw.p, h->P, h->lanes_csc, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
   lsq::launch_cg_update(h->n, h->P, h->part_pw.p, h->part_rz.p, h->p.p, h->w.p, h->x.p, h->r.p,
                         flex ? h->r_old.p : nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->ahist.p, h->hist_cap, st);
-  precond(h, h->r.p, h->z.p, 0, true, flex);
+  precond(h, h->r.p, h->z.p, 0, true, flex, timed);
   lsq::launch_p_update(h->n, h->P, h->part_rz.p, flex ? h->part_rzo.p : nullptr, h->part_rr.p, h->scal.p,
                        h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, st);
   CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
@@ -226,6 +238,24 @@ double dev_sum(ls_handle* h) {
   return v;
 }
 
+// ||g - C x||^2 into the host: mode 0 as ||A^T (b - A x)||^2, mode 1 as ||g - A^T (A x)||^2.
+// Leaves the residual vector in h->w; adds the kernels it launched to *launches.
+double true_residual(ls_handle* h, int mode, int* launches) {
+  cudaStream_t st = h->st;
+  lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+  if (mode == 0) {
+    lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
+    *launches += 4;
+  } else {
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
+    lsq::launch_axpby(h->n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
+    lsq::launch_dot(h->n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
+    *launches += 5;
+  }
+  return dev_sum(h);
+}
+
 // PCG on C x = g.  mode 0: g = A^T b with b in h->bv (true residual A^T (b - A x));
 // mode 1: g given in h->tv (true residual g - A^T A x).  Result in h->x.
 ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
@@ -233,6 +263,9 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   const int64_t n = h->n;
   const bool flex = h->prec != LS_PREC_F64;
   const double t0 = now_s();
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
   // r = g, gg = ||g||^2
   if (mode == 0) {
     lsq::launch_spmv_csc(csc(h), h->bv.p, h->r.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
@@ -241,16 +274,17 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     lsq::launch_dot(n, h->r.p, h->r.p, h->part_rr.p, h->P, st);
   }
   const double gg = dev_sum(h);
+  launches += 2;
   if (!std::isfinite(gg)) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
   const double gn = std::sqrt(gg);
   lsq::launch_fill(n, 0.0, h->x.p, st);
+  launches += 1;
   CK(cudaMemsetAsync(h->ctr.p, 0, sizeof(int), st));
   CK(cudaMemsetAsync(h->scal.p, 0, sizeof(double) * lsq::S_NSLOT, st));
-  ls_info inf{};
-  inf.bad_subdomain = -1;
   if (gn == 0.0) {
     CK(cudaStreamSynchronize(st));
     inf.t_solve = now_s() - t0;
+    inf.launches = launches;
     if (info) *info = inf;
     return LS_OK;
   }
@@ -258,11 +292,14 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     precond(h, h->r.p, h->z.p, 0, true, false);
     lsq::launch_p_update(n, h->P, h->part_rz.p, nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->bhist.p,
                          h->hist_cap, h->z.p, h->p.p, 1, st);
+    launches += iteration_launches(h) - 3;
+    inf.local_launches += 1;
   };
   restart();
   check_launch("initial preconditioner apply");
   const int fixed = h->opt.fixed_iters;
   const int maxit = fixed > 0 ? fixed : h->opt.maxit;
+  const bool timed = h->opt.time_kernels != 0;
   bool converged = false;
   int it = 0, restarts = 0;
   double rr = gg;
@@ -290,23 +327,23 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     CK(cudaStreamSynchronize(st));
     check_launch("CG iteration");
     ++it;
+    launches += iteration_launches(h);
+    inf.local_launches += 1;
+    if (timed) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+      CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
+      CK(cudaEventElapsedTime(&c, h->ev[3], h->ev[4]));
+      inf.ms_spmv += a;
+      inf.ms_local += b;
+      inf.ms_coarse += c;
+    }
     rr = h->pin[lsq::S_RR];
     if (h->pin[lsq::S_FLAG] != 0.0 || !std::isfinite(rr))
       throw LsError(LS_ERR_NONFINITE, "CG breakdown: non-finite or non-positive p.Cp at iteration " + std::to_string(it));
     if (fixed > 0) continue;
     if (std::sqrt(rr) <= rtol * gn) {
-      // true residual
-      if (mode == 0) {
-        lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
-        lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
-        lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
-      } else {
-        lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
-        lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
-        lsq::launch_axpby(n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
-        lsq::launch_dot(n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
-      }
-      const double tt = dev_sum(h);
+      const double tt = true_residual(h, mode, &launches);
       inf.relres_true = std::sqrt(tt) / gn;
       if (std::sqrt(tt) <= rtol * gn) { converged = true; break; }
       CK(cudaMemcpyAsync(h->r.p, h->w.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -318,19 +355,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   inf.iters = it;
   inf.restarts = restarts;
   inf.relres_recursive = std::sqrt(rr) / gn;
-  if (!converged) {
-    if (mode == 0) {
-      lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
-      lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
-      lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
-    } else {
-      lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
-      lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
-      lsq::launch_axpby(n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
-      lsq::launch_dot(n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
-    }
-    inf.relres_true = std::sqrt(dev_sum(h)) / gn;
-  }
+  if (!converged) inf.relres_true = std::sqrt(true_residual(h, mode, &launches)) / gn;
   inf.kappa_lanczos = 0.0;
   const int nh = std::min(it, h->hist_cap);
   if (restarts == 0 && nh > 0) {
@@ -349,6 +374,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.bad_subdomain = -1; inf.eig_steps_max = h->sinfo.eig_steps_max;
+  inf.launches = launches;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -671,6 +697,8 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->ahist.alloc(h->hist_cap); h->bhist.alloc(h->hist_cap);
   h->ctr.alloc(1);
   CK(cudaHostAlloc((void**)&h->pin, sizeof(double) * lsq::S_NSLOT, cudaHostAllocDefault));
+  if (h->opt.time_kernels)
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
   std::memset(h->pin, 0, sizeof(double) * lsq::S_NSLOT);
   CK(cudaStreamSynchronize(st));
   h->sinfo.t_setup = now_s() - t_begin;
@@ -694,6 +722,7 @@ void ls_default_options(ls_options* o) {
   o->eig_maxit = 3000;
   o->eig_tol = 1e-11;
   o->use_graph = 1;
+  o->time_kernels = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -858,6 +887,15 @@ ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap) 
         o[4 * s + 2] = h->h_xi_off[s + 1] - h->h_xi_off[s];
         o[4 * s + 3] = h->h_k.empty() ? 0 : h->h_k[s];
       }
+      return LS_OK;
+    }
+    if (kind == LS_Q_STORAGE) {
+      need(8);
+      int64_t* o = (int64_t*)out;
+      int64_t zel = 0;
+      for (int s = 0; s < N; ++s) zel += (int64_t)(h->h_k.empty() ? 0 : h->h_k[s]) * h->h_nI[s];
+      o[0] = h->fac_elems; o[1] = h->total_local; o[2] = h->total_blocks; o[3] = zel;
+      o[4] = h->n0; o[5] = h->n0p; o[6] = h->nnz; o[7] = h->prec;
       return LS_OK;
     }
     if (kind == LS_Q_EIGSTEPS) {

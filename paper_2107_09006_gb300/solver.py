@@ -8,7 +8,7 @@ import torch
 
 from . import (ls_setup, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info,
                ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI,
-               LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS)
+               LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE)
 
 
 def _dev(a, dtype, device):
@@ -25,7 +25,8 @@ class Solver:
     use_graph).  Arrays may be numpy arrays or tensors; they are copied by setup.
     """
 
-    def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", **options):
+    def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", stream=None, **options):
+        """``stream``: a torch.cuda.Stream the handle runs on (None: its own stream)."""
         self.device = torch.device(device)
         self.m, self.n = int(m), int(n)
         self.row_ptr = _dev(row_ptr, torch.int64, self.device)
@@ -35,7 +36,10 @@ class Solver:
         self.nparts = int(nparts)
         self.opt = ls_default_options(**options)
         with torch.cuda.device(self.device):
-            self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1, self.opt)
+            torch.cuda.synchronize(self.device)  # the inputs above were written on torch's stream
+            self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1, self.opt,
+                              stream.cuda_stream if stream is not None else None)
+        self.stream = stream
 
     def close(self):
         if getattr(self, "h", None):
@@ -51,11 +55,17 @@ class Solver:
     def info(self) -> dict:
         return ls_handle_info(self.h)
 
+    def _fence(self):
+        """Order torch's pending writes of the inputs before the library's stream reads them."""
+        if self.stream is None:
+            torch.cuda.current_stream(self.device).synchronize()
+
     def solve(self, b, rtol=1e-8, raise_on_fail=True):
         """x = argmin ||A x - b|| for b of shape [m] or [nrhs, m] (one right-hand side per row)."""
         b = _dev(b, torch.float64, self.device)
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         x = torch.empty((self.n,) if b.dim() == 1 else (nrhs, self.n), dtype=torch.float64, device=self.device)
+        self._fence()
         info = ls_solve(self.h, b, nrhs, rtol, x, raise_on_fail)
         return x, info
 
@@ -66,18 +76,21 @@ class Solver:
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         gb = torch.empty_like(b) if want_b else None
         gv = torch.empty(self.val.shape[0], dtype=torch.float64, device=self.device) if want_vals else None
+        self._fence()
         info = ls_backward(self.h, b, x, g, nrhs, rtol, gb, gv)
         return gb, gv, info
 
     def apply_preconditioner(self, r, which=0):
         r = _dev(r, torch.float64, self.device)
         z = torch.empty_like(r)
+        self._fence()
         ls_apply_preconditioner(self.h, r, z, which)
         return z
 
     def apply_normal(self, p):
         p = _dev(p, torch.float64, self.device)
         w = torch.empty_like(p)
+        self._fence()
         ls_apply_normal(self.h, p, w)
         return w
 
@@ -103,6 +116,11 @@ class Solver:
         if k:
             ls_query(self.h, LS_Q_ZBAR, i, out)
         return out[: k * nI].reshape(k, nI)
+
+    def storage(self) -> dict:
+        o = ls_query(self.h, LS_Q_STORAGE, 0, np.zeros(8, np.int64))
+        keys = ("fac_elems", "total_local", "total_blocks", "zbar_elems", "n0", "n0_padded", "nnz", "prec")
+        return {k: int(v) for k, v in zip(keys, o)}
 
     def eig_steps(self) -> np.ndarray:
         return ls_query(self.h, LS_Q_EIGSTEPS, 0, np.zeros(self.nparts, np.int32))

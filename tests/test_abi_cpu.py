@@ -1,0 +1,69 @@
+"""CPU-side checks of the C ABI library: it loads, exports every symbol the header
+declares, and its host-only index-set builder matches the oracle bit-exactly.
+No GPU compute is called here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2107_09006_gb300 as L
+    return L
+
+
+def test_every_declared_symbol_is_exported(lib):
+    hdr = open(os.path.join(ROOT, "include", "ls_schwarz.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+char\*|void|ls_status)\s+(ls_\w+)\s*\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    import ctypes
+    so = ctypes.CDLL(lib.LIBRARY_PATH)
+    for name in declared:
+        assert hasattr(so, name), name
+    assert declared == set(lib.EXPORTED)
+
+
+def test_default_options(lib):
+    o = lib.ls_default_options()
+    assert (o.nev_max, o.delta_rel, o.s_rel, o.maxit, o.coarse, o.use_graph) == (16, 1e-10, 1e-8, 1000, 1, 1)
+
+
+@pytest.mark.parametrize("which", ["tiny", "ragged", "example"])
+def test_host_index_sets_match_oracle(lib, which):
+    import oracle as O
+    from workloads import config_tiny, make_grid_ls, block_partition, paper_example, csr_from_dense
+    if which == "tiny":
+        P = config_tiny()
+        m, n, rp, c, v, part, N = P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts
+    elif which == "ragged":
+        m, n, rp, c, v, _, _ = make_grid_ls(37, 29, 3, 6, 2, 4)
+        part = block_partition(37, 29, 10, 7)
+        N = int(part.max()) + 1
+    else:
+        A, part = paper_example()
+        rp, c, v = csr_from_dense(A)
+        m, n, N = 5, 4, 2
+    om_off, om, nI, xi_off, xi = lib.ls_build_index_sets(m, n, rp, c, N, part)
+    S = O.index_sets(O.schwarz.as_csr(m, n, rp, c, v), part, N)
+    for i in range(N):
+        assert np.array_equal(om[om_off[i]:om_off[i + 1]], S.Om[i])
+        assert np.array_equal(xi[xi_off[i]:xi_off[i + 1]], S.Xi[i])
+        assert nI[i] == len(S.OI[i])
+
+
+def test_host_index_sets_reject_bad_input(lib):
+    from workloads import config_tiny
+    P = config_tiny()
+    bad = P.col.copy()
+    bad[0], bad[1] = bad[1], bad[0]
+    with pytest.raises(lib.LSError) as e:
+        lib.ls_build_index_sets(P.m, P.n, P.row_ptr, bad, P.nparts, P.part)
+    assert e.value.status == lib.LS_ERR_INVALID
+    with pytest.raises(lib.LSError):
+        lib.ls_build_index_sets(P.m, P.n, P.row_ptr, P.col, P.nparts, np.full(P.n, -1, np.int32))

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP64 form): the library and the oracle compute the same operators in a
+different summation order, so products and preconditioner applications agree to a
+few ulps times the condition of the operation: 1e-12 relative for A^T A p and the
+local solves, 1e-9 for the full two-level apply and 1e-10 for PCG iterates (the
+eigen-subspaces enter through Lanczos on the device and dense eigh in the oracle;
+their difference is bounded by eig_tol / (relative spectral gap)).  Integer work
+(index sets, coarse dimensions) is compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2107_09006_gb300 as L  # noqa: E402
+import oracle as O  # noqa: E402
+from workloads import (config_tiny, make_grid_ls, block_partition, strip_partition,  # noqa: E402
+                       paper_example, csr_from_dense, bisection_partition)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+class Case:
+    def __init__(self, name, m, n, rp, c, v, b, part, N, nev=16, tau=0.0):
+        self.name, self.m, self.n, self.rp, self.c, self.v, self.b, self.part, self.N = name, m, n, rp, c, v, b, part, N
+        self.nev, self.tau = nev, tau
+        self.A = O.schwarz.as_csr(m, n, rp, c, v)
+        self._M = None
+
+    def solver(self, **kw):
+        opts = dict(nev_max=self.nev, tau=self.tau)
+        opts.update(kw)
+        return L.Solver(self.m, self.n, self.rp, self.c, self.v, self.part, self.N, **opts)
+
+    def oracle(self, coarse=True):
+        return O.build_two_level(self.A, self.part, self.N, tau=self.tau, nev_max=self.nev, coarse=coarse)
+
+
+def _tiny():
+    P = config_tiny()
+    return Case("tiny", P.m, P.n, P.row_ptr, P.col, P.val, P.b, P.part, P.nparts)
+
+
+def _mid():
+    # several 32-row tiles per subdomain and a ragged last tile (n_i not a multiple of 32)
+    m, n, rp, c, v, b, _ = make_grid_ls(96, 96, 4, 8, 3, 0)
+    return Case("grid96-N9", m, n, rp, c, v, b, block_partition(96, 96, 32, 32), 9)
+
+
+def _uneven():
+    m, n, rp, c, v, b, _ = make_grid_ls(60, 52, 4, 6, 2, 5)
+    part = bisection_partition(60, 52, 700, 9)
+    return Case("bisect-uneven", m, n, rp, c, v, b, part, int(part.max()) + 1, nev=8)
+
+
+def _example():
+    A, part = paper_example()
+    rp, c, v = csr_from_dense(A)
+    return Case("paper-example", 5, 4, rp, c, v, np.arange(1.0, 6.0), part, 2, nev=2, tau=0.6)
+
+
+CASES = {"tiny": _tiny, "mid": _mid, "uneven": _uneven, "example": _example}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    return CASES[request.param]()
+
+
+def test_index_sets_bit_exact(case):
+    S = case.solver(coarse=0)
+    M = O.index_sets(case.A, case.part, case.N)
+    for i in range(case.N):
+        assert np.array_equal(S.omega(i), M.Om[i])
+        assert np.array_equal(S.xi(i), M.Xi[i])
+    S.close()
+
+
+def test_normal_product(case):
+    S = case.solver(coarse=0)
+    p = np.random.default_rng(1).standard_normal(case.n)
+    w = S.apply_normal(p).cpu().numpy()
+    assert rel(w, case.A.T @ (case.A @ p)) < 1e-13
+    S.close()
+
+
+def test_one_level_apply(case):
+    S = case.solver(coarse=0)
+    M = case.oracle(coarse=False)
+    r = np.random.default_rng(2).standard_normal(case.n)
+    assert rel(S.apply_preconditioner(r, 1).cpu().numpy(), M.apply_local(r)) < 1e-12
+    S.close()
+
+
+def test_eigenvalues_and_coarse_dimension(case):
+    S = case.solver()
+    M = case.oracle()
+    for i in range(case.N):
+        lg = S.eigvals(i)
+        lo = M.lams[i][: len(lg)]
+        assert np.max(np.abs(lg - lo)) <= 1e-10 * max(1.0, np.abs(lo).max())
+    assert S.sizes()[:, 3].tolist() == list(M.ks)
+    assert S.info()["n0"] == M.n0
+    S.close()
+
+
+def test_two_level_apply(case):
+    S = case.solver()
+    M = case.oracle()
+    r = np.random.default_rng(3).standard_normal(case.n)
+    assert rel(S.apply_preconditioner(r, 0).cpu().numpy(), M.apply(r)) < 1e-9
+    assert rel(S.apply_preconditioner(r, 2).cpu().numpy(), M.apply_coarse(r)) < 1e-8
+    S.close()
+
+
+def test_coarse_span_matches(case):
+    """The device coarse basis spans the oracle's (compared through projectors)."""
+    S = case.solver()
+    M = case.oracle()
+    Rg = M.R0T.toarray()
+    if Rg.shape[1] == 0:
+        pytest.skip("empty coarse space")
+    Zd = [S.zbar(i) for i in range(case.N)]
+    Rd = np.zeros_like(Rg)
+    off = 0
+    for i, Z in enumerate(Zd):
+        k = Z.shape[0]
+        Rd[M.S.OI[i], off:off + k] = Z.T
+        off += k
+    Qg, _ = np.linalg.qr(Rg)
+    Qd, _ = np.linalg.qr(Rd)
+    assert np.linalg.norm(Qg @ Qg.T - Qd @ Qd.T, 2) < 1e-7
+    S.close()
+
+
+def test_pcg_fixed_iterations(case):
+    S = case.solver(fixed_iters=6)
+    M = case.oracle()
+    x, _ = S.solve(case.b, rtol=1e-8)
+    xo, _ = O.pcg(case.A, case.b, M.apply, fixed_iters=6)
+    assert rel(x.cpu().numpy(), xo) < 1e-10
+    S.close()
+
+
+def test_pcg_converged(case):
+    S = case.solver()
+    M = case.oracle()
+    x, info = S.solve(case.b, rtol=1e-8)
+    xo, io = O.pcg(case.A, case.b, M.apply, rtol=1e-8)
+    assert info["relres_true"] <= 1e-8
+    assert abs(info["iters"] - io["iters"]) <= 1
+    x13, i13 = S.solve(case.b, rtol=1e-13)
+    xo13, _ = O.pcg(case.A, case.b, M.apply, rtol=1e-13)
+    assert rel(x13.cpu().numpy(), xo13) < 1e-10
+    if i13["restarts"] == 0 and case.n > 10:
+        assert abs(i13["kappa_lanczos"] - O.lanczos_kappa(*_coeffs(case, M))) < 1e-6 * i13["kappa_lanczos"]
+    S.close()
+
+
+def _coeffs(case, M):
+    _, io = O.pcg(case.A, case.b, M.apply, rtol=1e-13)
+    return io["alphas"], io["betas"]
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-8), ("bf16", 1e-8)])
+def test_mixed_forms_meet_tolerance(prec, tol):
+    c = _mid()
+    S = c.solver(factor_prec=prec)
+    x, info = S.solve(c.b, rtol=tol)
+    assert info["relres_true"] <= tol
+    M = c.oracle()
+    xo, _ = O.pcg(c.A, c.b, M.apply, rtol=1e-13)
+    # error against the FP64 solution is bounded by kappa(C) times the residual tolerance
+    kappa = np.linalg.cond(c.A.toarray()) ** 2
+    assert rel(x.cpu().numpy(), xo) <= kappa * tol
+    S.close()
+
+
+def test_one_subdomain_exact():
+    c = _tiny()
+    c.part = np.zeros(c.n, np.int32)
+    c.N = 1
+    c.tau = 0.6
+    S = c.solver()
+    assert S.info()["n0"] == 0
+    x, info = S.solve(c.b, rtol=1e-8)
+    assert info["iters"] <= 3
+    S.close()
+
+
+def test_backward_against_dense_gradient():
+    c = _tiny()
+    S = c.solver()
+    x, _ = S.solve(c.b, rtol=1e-13)
+    xs = np.random.default_rng(7).standard_normal(c.n)
+    gx = 2 * (x.cpu().numpy() - xs)
+    gb, gv, _ = S.backward(c.b, x, gx, rtol=1e-13)
+    Ad = c.A.toarray()
+    C = Ad.T @ Ad
+    xd = np.linalg.solve(C, Ad.T @ c.b)
+    gbo, gvo, _ = O.adjoint_gradient(c.A, c.b, xd, 2 * (xd - xs), lambda g: np.linalg.solve(C, g))
+    assert rel(gb.cpu().numpy(), gbo) < 1e-9
+    assert rel(gv.cpu().numpy(), gvo) < 1e-9
+    S.close()
+
+
+def test_errors_are_reported():
+    c = _tiny()
+    with pytest.raises(L.LSError) as e:
+        L.Solver(c.m, c.n, c.rp, c.c, c.v, np.full(c.n, 99, np.int32), c.N)
+    assert e.value.status == L.LS_ERR_INVALID
+    bad = c.c.copy()
+    bad[1], bad[2] = bad[2], bad[1]  # unsorted row
+    with pytest.raises(L.LSError) as e:
+        L.Solver(c.m, c.n, c.rp, bad, c.v, c.part, c.N)
+    assert e.value.status == L.LS_ERR_INVALID
+    v = c.v.copy()
+    v[3] = np.nan
+    with pytest.raises(L.LSError) as e:
+        L.Solver(c.m, c.n, c.rp, c.c, v, c.part, c.N)
+    assert e.value.status == L.LS_ERR_NONFINITE
+    S = c.solver(maxit=2)
+    x, info = S.solve(c.b, rtol=1e-12, raise_on_fail=False)
+    assert info["status"] == L.LS_ERR_NOT_CONVERGED and info["iters"] == 2
+    S.close()
