@@ -129,8 +129,8 @@ struct ls_handle {
   DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
   DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
   DevBuf<uint8_t> om_int;
-  DevBuf<double> eqs, L64, idiag64;
-  DevBuf<float> L32, idiag32, tsc;
+  DevBuf<double> eqs, L64;
+  DevBuf<float> L32, tsc;
   DevBuf<__nv_bfloat16> L16;
   int max_nb = 0;
   int64_t total_local = 0, total_blocks = 0, fac_elems = 0;
@@ -191,7 +191,7 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
     a.fac = h->prec == LS_PREC_F64 ? (const void*)h->L64.p
           : h->prec == LS_PREC_F32 ? (const void*)h->L32.p : (const void*)h->L16.p;
     a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
-    a.idiag = h->prec == LS_PREC_F64 ? (const void*)h->idiag64.p : (const void*)h->idiag32.p;
+    a.err = h->scal.p + lsq::S_ERR;
     a.r = rin; a.y = h->ybuf.p;
     a.coarse = use_coarse ? 1 : 0;
     a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
@@ -339,6 +339,9 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
       inf.ms_coarse += c;
     }
     rr = h->pin[lsq::S_RR];
+    if (h->pin[lsq::S_ERR] != 0.0)
+      throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up at iteration " +
+                                               std::to_string(it));
     if (h->pin[lsq::S_FLAG] != 0.0 || !std::isfinite(rr))
       throw LsError(LS_ERR_NONFINITE, "CG breakdown: non-finite or non-positive p.Cp at iteration " + std::to_string(it));
     if (fixed > 0) continue;
@@ -513,12 +516,12 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   Bst.alloc(h->fac_elems);  // prep always writes B = C~_ii + s I
   lsq::launch_prep(plan, delta, sdev.p, Cst.p, h->eqs.p, Ctst.p, Bst.p, st);
   check_launch("prep");
-  DevBuf<double> dinv, Bidiag;
+  DevBuf<double> dinv, Bidiag, idiag;
   DevBuf<int> status;
   dinv.alloc((size_t)h->total_blocks * 1024);
   status.alloc(N);
-  h->idiag64.alloc((size_t)h->total_blocks * 32);
-  lsq::launch_band_cholesky(plan, Cst.p, h->idiag64.p, dinv.p, status.p, st);
+  idiag.alloc((size_t)h->total_blocks * 32);
+  lsq::launch_band_cholesky(plan, Cst.p, idiag.p, dinv.p, status.p, st);
   std::vector<int> hst(N);
   CK(cudaMemcpyAsync(hst.data(), status.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -529,6 +532,24 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
       throw LsError(LS_ERR_FACTOR, "Cholesky of C_ii failed in subdomain " + std::to_string(i) + " at local row " +
                                        std::to_string(hst[i] - 1));
     }
+  // solve storage in the factor precision: column-major panels + inverse diagonal tiles
+  h->prec = h->opt.factor_prec;
+  {
+    void* dst = nullptr;
+    if (h->prec == LS_PREC_F64) { h->L64.alloc(h->fac_elems); dst = h->L64.p; }
+    else if (h->prec == LS_PREC_F32) { h->L32.alloc(h->fac_elems); dst = h->L32.p; }
+    else {
+      h->L16.alloc(h->fac_elems);
+      h->tsc.alloc(std::max<int64_t>(h->fac_elems / 1024, 1));
+      dst = h->L16.p;
+    }
+    lsq::launch_to_solve_layout(h->prec, h->total_blocks, h->blk_poff.p, Cst.p, dinv.p, dst,
+                                h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr, st);
+    CK(cudaStreamSynchronize(st));
+    check_launch("solve storage");
+    Cst.release();
+    idiag.release();
+  }
 
   h->sinfo.delta = delta;
   h->kwant_cap = h->opt.nev_max + 1;
@@ -665,25 +686,6 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   }
   Bst.release(); Ctst.release(); Bidiag.release();
 
-  // factor precision of the solve
-  h->prec = h->opt.factor_prec;
-  if (h->prec == LS_PREC_F64) {
-    h->L64.p = Cst.p; h->L64.n = Cst.n; Cst.p = nullptr; Cst.n = 0;
-  } else {
-    h->idiag32.alloc((size_t)h->total_blocks * 32);
-    lsq::launch_convert_f32(h->total_blocks * 32, h->idiag64.p, h->idiag32.p, st);
-    if (h->prec == LS_PREC_F32) {
-      h->L32.alloc(h->fac_elems);
-      lsq::launch_convert_f32(h->fac_elems, Cst.p, h->L32.p, st);
-    } else {
-      h->L16.alloc(h->fac_elems);
-      h->tsc.alloc(std::max<int64_t>(h->fac_elems / 1024, 1));
-      lsq::launch_convert_bf16(h->total_blocks, h->blk_poff.p, Cst.p, h->L16.p, h->tsc.p, st);
-    }
-    CK(cudaStreamSynchronize(st));
-    Cst.release();
-    h->idiag64.release();
-  }
   // work vectors
   const int64_t mm = std::max(h->m, h->n);
   h->x.alloc(h->n); h->r.alloc(h->n); h->r_old.alloc(h->n); h->z.alloc(h->n); h->p.alloc(h->n);

@@ -83,6 +83,8 @@ std::string build_host_sets(int64_t m, int64_t n, const int64_t* row_ptr, const 
   std::vector<int64_t> ioff(N + 1, 0);
   for (int64_t j = 0; j < n; ++j) ioff[part[j] + 1]++;
   for (int i = 0; i < N; ++i) ioff[i + 1] += ioff[i];
+  for (int i = 0; i < N; ++i)
+    if (ioff[i + 1] == ioff[i]) return "subdomain " + std::to_string(i) + " owns no column";
   std::vector<int32_t> interior(n);
   hs.jj_of.resize(n);
   {

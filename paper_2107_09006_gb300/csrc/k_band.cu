@@ -187,80 +187,6 @@ __global__ void __launch_bounds__(kThreads) k_band_cholesky(BandPlan P, double* 
   if (threadIdx.x == 0) status[i] = fail;
 }
 
-__global__ void k_convert_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    dst[k] = (float)src[k];
-}
-
-// One CTA per block row: per 32x32 tile, scale = max |entry| (1 if the tile is zero)
-// and the BF16 values entry / scale.
-__global__ void __launch_bounds__(kThreads) k_convert_bf16(const int64_t* __restrict__ poff, const double* __restrict__ src,
-                                                           __nv_bfloat16* __restrict__ dst, float* __restrict__ tsc) {
-  __shared__ double red[kWarps];
-  const int64_t g = blockIdx.x;
-  const int64_t po = poff[g];
-  const int width = (int)((poff[g + 1] - po) / kT);
-  const int ntile = width / kT;
-  for (int t = 0; t < ntile; ++t) {
-    double mx = 0.0;
-    for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
-      const int rr = e >> 5, cc = e & 31;
-      mx = fmax(mx, fabs(src[po + (int64_t)rr * width + t * kT + cc]));
-    }
-    // block max through the sum helper on a one-hot trick is not possible; do it directly
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    double m = 0.0;
-    for (int k = 0; k < kWarps; ++k) m = fmax(m, red[k]);
-    const double sc = m > 0.0 ? m : 1.0;
-    if (threadIdx.x == 0) tsc[po / 1024 + t] = (float)sc;
-    for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
-      const int rr = e >> 5, cc = e & 31;
-      const int64_t idx = po + (int64_t)rr * width + t * kT + cc;
-      dst[idx] = __float2bfloat16_rn((float)(src[idx] / sc));
-    }
-  }
-}
-
-// One CTA per subdomain: gather r(Omega_i), optional coarse restriction
-// r0_i = Zbar_i^T r(Omega_I,i), then C_ii^{-1} through the (equilibrated) factor.
-template <class TF, class TA>
-__global__ void __launch_bounds__(kThreads) k_local_solve(LocalArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int i = blockIdx.x;
-  const int64_t o0 = a.om_off[i];
-  const int ni = (int)(a.om_off[i + 1] - o0);
-  const int64_t b0 = a.blk_off[i];
-  const int nb = (int)(a.blk_off[i + 1] - b0);
-  TA* v = reinterpret_cast<TA*>(smem_raw);
-  TA* dt = v + nb * kT;
-  TA* tmp = dt + kT * 33;
-  for (int k = threadIdx.x; k < nb * kT; k += blockDim.x)
-    v[k] = k < ni ? (TA)(a.r[a.om_glob[o0 + k]] * a.eqs[o0 + k]) : (TA)0;
-  if (a.coarse) {
-    const int c0 = a.coff[i], kk = a.coff[i + 1] - c0;
-    const int64_t io = a.int_off[i];
-    const int nIi = (int)(a.int_off[i + 1] - io);
-    const double* Zi = a.Z + a.zoff[i];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int t = w; t < kk; t += kWarps) {
-      double acc = 0.0;
-      for (int jj = lane; jj < nIi; jj += 32) acc += Zi[(int64_t)t * nIi + jj] * a.r[a.int_glob[io + jj]];
-      acc = warp_sum(acc);
-      if (lane == 0) a.r0[c0 + t] = acc;
-    }
-  }
-  __syncthreads();
-  BandRef B{a.blk_tf + b0, a.blk_poff + b0, nb};
-  const TF* fac = reinterpret_cast<const TF*>(a.fac);
-  const TA* idg = reinterpret_cast<const TA*>(a.idiag) + b0 * kT;
-  band_forward<TF, TA>(fac, a.tsc, idg, B, v, dt, tmp);
-  band_backward<TF, TA>(fac, a.tsc, idg, B, v, dt, tmp);
-  for (int k = threadIdx.x; k < ni; k += blockDim.x) a.y[o0 + k] = (double)v[k] * a.eqs[o0 + k];
-}
-
 int grid_for(int64_t work, int cap) {
   int64_t g = (work + kThreads - 1) / kThreads;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -286,39 +212,6 @@ void launch_prep(const BandPlan& P, double delta, const double* s, double* Cst, 
 void launch_band_cholesky(const BandPlan& P, double* F, double* idiag, double* dinv, int* status,
                                cudaStream_t st) {
   k_band_cholesky<<<P.N, kThreads, 0, st>>>(P, F, idiag, dinv, status);
-}
-
-void launch_convert_f32(int64_t n, const double* src, float* dst, cudaStream_t st) {
-  k_convert_f32<<<grid_for(n, 8192), kThreads, 0, st>>>(n, src, dst);
-}
-
-void launch_convert_bf16(int64_t nblocks, const int64_t* poff, const double* src, __nv_bfloat16* dst,
-                              float* tsc, cudaStream_t st) {
-  k_convert_bf16<<<(unsigned)nblocks, kThreads, 0, st>>>(poff, src, dst, tsc);
-}
-
-size_t local_solve_smem(int prec, int max_nb) {
-  const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
-  return es * ((size_t)max_nb * kT + kT * 33 + kT);
-}
-
-void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
-  // The opt-in shared-memory limit is raised only when a larger size is first needed,
-  // so launches inside a stream capture make no attribute calls.
-  static size_t raised[3] = {0, 0, 0};
-  const size_t sm = local_solve_smem(prec, max_nb);
-  const bool raise = sm > 48 * 1024 && sm > raised[prec];
-  if (prec == 0) {
-    if (raise) cudaFuncSetAttribute(k_local_solve<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_local_solve<double, double><<<N, kThreads, sm, st>>>(a);
-  } else if (prec == 1) {
-    if (raise) cudaFuncSetAttribute(k_local_solve<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_local_solve<float, float><<<N, kThreads, sm, st>>>(a);
-  } else {
-    if (raise) cudaFuncSetAttribute(k_local_solve<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_local_solve<__nv_bfloat16, float><<<N, kThreads, sm, st>>>(a);
-  }
-  if (raise) raised[prec] = sm;
 }
 
 }  // namespace lsq

@@ -1,0 +1,345 @@
+// Batched local solves of the preconditioner apply: y_i = C_ii^{-1} R_i r for every
+// subdomain in one launch (one CTA per subdomain), plus the fused coarse restriction
+// r0_i = Zbar_i^T r(Omega_I,i).
+//
+// Solve storage.  The factor L_i of the (equilibrated) C_ii is kept block row by
+// block row (32 rows each); block row b is one contiguous segment of width columns
+// of 32 entries (column-major): first the off-diagonal panel L(b, tf_b .. b-1)
+// (offw = width - 32 columns), then the inverse of the diagonal tile L(b,b)^{-1}.
+// With the inverse tile, each block step is two dense products:
+//   forward  v_b <- L_bb^{-1} (v_b - L_off v_window)
+//   backward x_b  = L_bb^{-T} v_b ;  v_window -= L_off^T x_b
+// Streaming.  Each CTA reads its segments through a ring of 16 KB shared-memory
+// stages filled by bulk asynchronous copies (cp.async.bulk + mbarrier): the forward
+// sweep reads the subdomain's storage front to back, the backward sweep back to
+// front (each segment's chunks from its end, so the inverse tile arrives first).
+// The copies run ahead of the dependency chain of the block steps.  Every wait on a
+// stage is bounded; on timeout the kernel sets the error slot and returns.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lsq {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+template <class TF> struct Val;
+template <> struct Val<double> { static __device__ __forceinline__ double f(double x) { return x; } };
+template <> struct Val<float> { static __device__ __forceinline__ float f(float x) { return x; } };
+template <> struct Val<__nv_bfloat16> {
+  static __device__ __forceinline__ float f(__nv_bfloat16 x) { return __bfloat162float(x); }
+};
+
+constexpr int kStageBytes = 16384;
+constexpr long long kWaitCycles = 4000000000ll;  // about two seconds at GB300 clocks
+
+// Order of the chunks one CTA consumes: forward sweep, blocks ascending, each segment's
+// chunks from its start; backward sweep, blocks descending, each segment's chunks from
+// its end.  Chunk k of a segment (counted from its end) covers the columns
+// [max(0, width - (k+1) CC), width - k CC).
+struct ChunkIter {
+  int sweep, b, k, nb;
+  const int32_t* tf;
+  int CC;
+  __device__ int width(int bb) const { return (bb - tf[bb] + 1) * kT; }
+  __device__ int nchunks(int bb) const { return (width(bb) + CC - 1) / CC; }
+  __device__ void start(const int32_t* tf_, int nb_, int cc) {
+    tf = tf_; nb = nb_; CC = cc; sweep = 0; b = 0; k = nchunks(0) - 1;
+  }
+  __device__ bool done() const { return sweep == 1 && b < 0; }
+  __device__ void next() {
+    if (sweep == 0) {
+      if (k > 0) { --k; return; }
+      if (++b < nb) { k = nchunks(b) - 1; return; }
+      sweep = 1; b = nb - 1; k = 0;
+      return;
+    }
+    if (k + 1 < nchunks(b)) { ++k; return; }
+    --b; k = 0;
+  }
+};
+
+template <class TF, class TA, int S>
+__global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int ES = sizeof(TF);
+  constexpr int CC = kStageBytes / (kT * ES);  // columns per stage
+  constexpr int CHUNK = CC * kT;                // elements per stage
+  TF* ring = reinterpret_cast<TF*>(smem_raw);
+  TA* red = reinterpret_cast<TA*>(smem_raw + S * kStageBytes);
+  TA* tv = red + kWarps * 32;
+  TA* xv = tv + 32;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xv + 32);
+  int* abort_flag = reinterpret_cast<int*>(bars + S);
+  TA* v = reinterpret_cast<TA*>(bars + S + 1);
+
+  const int i = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t o0 = a.om_off[i];
+  const int ni = (int)(a.om_off[i + 1] - o0);
+  const int64_t b0 = a.blk_off[i];
+  const int nb = (int)(a.blk_off[i + 1] - b0);
+  const int32_t* tf = a.blk_tf + b0;
+  const int64_t* poff = a.blk_poff + b0;
+  const TF* fac = reinterpret_cast<const TF*>(a.fac);
+  if (nb == 0) return;  // (the host rejects empty subdomains; kept as a guard)
+
+  ChunkIter prod, cons;
+  int issued = 0;  // chunks issued so far (thread 0)
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int stage) {
+    const int wd = prod.width(prod.b);
+    const int hi = wd - prod.k * CC;
+    const int lo = max(0, hi - CC);
+    const uint32_t bytes = (uint32_t)((hi - lo) * kT * ES);
+    fence_proxy_async();
+    mbar_expect_tx(&bars[stage], bytes);
+    bulk_g2s(ring + stage * CHUNK, fac + poff[prod.b] + (int64_t)lo * kT, bytes, &bars[stage]);
+    prod.next();
+    ++issued;
+  };
+  if (tid == 0) {
+    prod.start(tf, nb, CC);
+    for (int s = 0; s < S - 1 && !prod.done(); ++s) issue(s);
+  }
+  // gather r(Omega_i), scaled by the equilibration, while the first stages load
+  for (int k = tid; k < nb * kT; k += blockDim.x)
+    v[k] = k < ni ? (TA)(a.r[a.om_glob[o0 + k]] * a.eqs[o0 + k]) : (TA)0;
+  if (a.coarse) {
+    const int c0 = a.coff[i], kk = a.coff[i + 1] - c0;
+    const int64_t io = a.int_off[i];
+    const int nIi = (int)(a.int_off[i + 1] - io);
+    const double* Zi = a.Z + a.zoff[i];
+    for (int t = w; t < kk; t += kWarps) {
+      double acc = 0.0;
+      for (int jj = lane; jj < nIi; jj += 32) acc += Zi[(int64_t)t * nIi + jj] * a.r[a.int_glob[io + jj]];
+      acc = warp_sum(acc);
+      if (lane == 0) a.r0[c0 + t] = acc;
+    }
+  }
+  __syncthreads();
+
+  cons.start(tf, nb, CC);
+  TA acc = 0;
+  int q = 0;
+  while (!cons.done()) {
+    const int stage = q % S;
+    if (tid == 0 && !prod.done()) issue((q + S - 1) % S);
+    {
+      const uint32_t parity = (uint32_t)((q / S) & 1);
+      if (!mbar_try_wait(&bars[stage], parity)) {
+        const long long t0 = clock64();
+        bool ok = false;
+        while (!(ok = mbar_try_wait(&bars[stage], parity)))
+          if (clock64() - t0 > kWaitCycles) break;
+        if (!ok) *abort_flag = 1;
+      }
+    }
+    const TF* ch = ring + stage * CHUNK;
+    const int b = cons.b;
+    const int t0 = tf[b];
+    const int wd = (b - t0 + 1) * kT;
+    const int offw = wd - kT;
+    const int hi = wd - cons.k * CC;
+    const int lo = max(0, hi - CC);
+    const int phi = min(hi, offw);  // panel columns of this chunk: [lo, phi)
+    const float* sc = a.tsc ? a.tsc + poff[b] / 1024 : nullptr;
+    if (cons.sweep == 0) {
+      if (cons.k == cons.nchunks(b) - 1) acc = 0;
+      TA* vw = v + t0 * kT;
+      for (int c = lo + w; c < phi; c += kWarps) {
+        TA p = Val<TF>::f(ch[(c - lo) * kT + lane]);
+        if (sc) p *= (TA)sc[c >> 5];
+        acc += p * vw[c];
+      }
+      if (cons.k == 0) {
+        red[w * 32 + lane] = acc;
+        __syncthreads();
+        if (w == 0) {
+          TA s = 0;
+#pragma unroll
+          for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+          tv[lane] = v[b * kT + lane] - s;
+          __syncwarp();
+          const TF* D = ch + (offw - lo) * kT;  // inverse tile, column-major
+          const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
+          TA x = 0;
+#pragma unroll 8
+          for (int c = 0; c < kT; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
+          v[b * kT + lane] = x * dsc;
+        }
+      }
+    } else {
+      if (cons.k == 0) {
+        if (w == 0) {
+          tv[lane] = v[b * kT + lane];
+          __syncwarp();
+          const TF* D = ch + (offw - lo) * kT;
+          const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
+          TA x = 0;
+#pragma unroll 8
+          for (int u = 0; u < kT; ++u) {
+            const int r = (u + lane) & 31;  // skewed walk: no bank conflicts
+            x += Val<TF>::f(D[lane * kT + r]) * tv[r];
+          }
+          x *= dsc;
+          xv[lane] = x;
+          v[b * kT + lane] = x;
+        }
+        __syncthreads();
+      }
+      TA* vw = v + t0 * kT;
+      for (int c = lo + tid; c < phi; c += blockDim.x) {
+        const TF* col = ch + (c - lo) * kT;
+        TA s = 0;
+#pragma unroll 8
+        for (int u = 0; u < kT; ++u) {
+          const int r = (u + c) & 31;
+          s += Val<TF>::f(col[r]) * xv[r];
+        }
+        if (sc) s *= (TA)sc[c >> 5];
+        vw[c] -= s;
+      }
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    cons.next();
+    ++q;
+  }
+  if (*abort_flag) {
+    if (tid == 0) {
+      a.err[0] = 1.0;
+      // bounded drain of the copies still in flight before the CTA's shared memory is released
+      for (int qq = q; qq < issued; ++qq) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&bars[qq % S], (uint32_t)((qq / S) & 1)))
+          if (clock64() - t0 > kWaitCycles) break;
+      }
+    }
+    return;
+  }
+  for (int k = tid; k < ni; k += blockDim.x) a.y[o0 + k] = (double)v[k] * a.eqs[o0 + k];
+}
+
+// Block-envelope factor (row-major panels, diagonal tile last) + inverse diagonal
+// tiles (row-major, FP64) -> solve storage of the given precision (see above).
+template <class TF>
+__global__ void __launch_bounds__(kThreads) k_to_solve_layout(const int64_t* __restrict__ poff,
+                                                              const double* __restrict__ L,
+                                                              const double* __restrict__ dinv, TF* __restrict__ dst,
+                                                              float* __restrict__ tsc) {
+  (void)tsc;
+  const int64_t g = blockIdx.x;
+  const int64_t po = poff[g];
+  const int width = (int)((poff[g + 1] - po) / kT);
+  const int offw = width - kT;
+  for (int64_t e = threadIdx.x; e < (int64_t)width * kT; e += blockDim.x) {
+    const int c = (int)(e >> 5), r = (int)(e & 31);
+    const double val = c < offw ? L[po + (int64_t)r * width + c] : dinv[g * 1024 + r * 32 + (c - offw)];
+    dst[po + e] = (TF)val;
+  }
+}
+
+template <>
+__global__ void __launch_bounds__(kThreads) k_to_solve_layout<__nv_bfloat16>(const int64_t* __restrict__ poff,
+                                                                             const double* __restrict__ L,
+                                                                             const double* __restrict__ dinv,
+                                                                             __nv_bfloat16* __restrict__ dst,
+                                                                             float* __restrict__ tsc) {
+  __shared__ double red[kWarps];
+  const int64_t g = blockIdx.x;
+  const int64_t po = poff[g];
+  const int width = (int)((poff[g + 1] - po) / kT);
+  const int offw = width - kT;
+  auto src = [&](int c, int r) -> double {
+    return c < offw ? L[po + (int64_t)r * width + c] : dinv[g * 1024 + r * 32 + (c - offw)];
+  };
+  for (int t = 0; t < width / kT; ++t) {
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) mx = fmax(mx, fabs(src(t * kT + (e >> 5), e & 31)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double m = 0.0;
+    for (int k = 0; k < kWarps; ++k) m = fmax(m, red[k]);
+    const double sc = m > 0.0 ? m : 1.0;
+    if (threadIdx.x == 0) tsc[po / 1024 + t] = (float)sc;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      const int c = t * kT + (e >> 5), r = e & 31;
+      dst[po + (int64_t)c * kT + r] = __float2bfloat16_rn((float)(src(c, r) / sc));
+    }
+    __syncthreads();
+  }
+}
+
+template <class TF, class TA, int S>
+size_t smem_bytes(int max_nb) {
+  return (size_t)S * kStageBytes + (kWarps * 32 + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) +
+         (size_t)max_nb * kT * sizeof(TA);
+}
+
+template <class TF, class TA, int S>
+void launch_impl(int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
+  static size_t raised = 0;
+  const size_t sm = smem_bytes<TF, TA, S>(max_nb);
+  if (sm > 48 * 1024 && sm > raised) {
+    cudaFuncSetAttribute(k_local_solve<TF, TA, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raised = sm;
+  }
+  k_local_solve<TF, TA, S><<<N, kThreads, sm, st>>>(a);
+}
+
+}  // namespace
+
+size_t local_solve_smem(int prec, int max_nb) {
+  if (prec == 0) return smem_bytes<double, double, 3>(max_nb);
+  if (prec == 1) return smem_bytes<float, float, 4>(max_nb);
+  return smem_bytes<__nv_bfloat16, float, 4>(max_nb);
+}
+
+void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
+  if (prec == 0) launch_impl<double, double, 3>(N, max_nb, a, st);
+  else if (prec == 1) launch_impl<float, float, 4>(N, max_nb, a, st);
+  else launch_impl<__nv_bfloat16, float, 4>(N, max_nb, a, st);
+}
+
+void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,
+                            void* dst, float* tsc, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  if (prec == 0) k_to_solve_layout<double><<<(unsigned)nblocks, kThreads, 0, st>>>(poff, L, dinv, (double*)dst, nullptr);
+  else if (prec == 1) k_to_solve_layout<float><<<(unsigned)nblocks, kThreads, 0, st>>>(poff, L, dinv, (float*)dst, nullptr);
+  else k_to_solve_layout<__nv_bfloat16><<<(unsigned)nblocks, kThreads, 0, st>>>(poff, L, dinv, (__nv_bfloat16*)dst, tsc);
+}
+
+}  // namespace lsq

@@ -11,7 +11,7 @@ struct CsrDev { int64_t m, n; const int64_t* row_ptr; const int32_t* col; const 
 struct CscDev { int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val; };
 
 // Scalar slots of the CG state kept on the device.
-enum { S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_NSLOT = 8 };
+enum { S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_ERR = 6, S_NSLOT = 8 };
 
 void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, cudaStream_t st);
 // w = A^T q; if part != nullptr also writes per-block partial sums of d.w (d = w if d == nullptr).
@@ -67,21 +67,23 @@ void launch_prep(const BandPlan& P, double delta, const double* s, double* Cst, 
 // dinv: scratch of 1024 doubles per block row (inverse diagonal tiles).
 void launch_band_cholesky(const BandPlan& P, double* st_fac, double* idiag, double* dinv, int* status,
                           cudaStream_t st);
-void launch_convert_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
-// One CTA per block row; poff has (number of block rows + 1) entries.
-void launch_convert_bf16(int64_t nblocks, const int64_t* poff, const double* src, __nv_bfloat16* dst,
-                         float* tsc, cudaStream_t st);
 
+// ---- batched local solves (k_local.cu) -----------------------------------------------
 struct LocalArgs {
   const int64_t* om_off; const int32_t* om_glob; const double* eqs;
   const int64_t* blk_off; const int32_t* blk_tf; const int64_t* blk_poff;
-  const void* fac; const float* tsc; const void* idiag;  // idiag: double (F64) or float
+  const void* fac; const float* tsc;  // solve storage (see k_local.cu); tsc: BF16 tile scales
   const double* r; double* y;
   int coarse; const int64_t* int_off; const int32_t* int_glob; const int64_t* zoff;
   const int32_t* coff; const double* Z; double* r0;
+  double* err;  // set to 1 when a bounded wait on a copy gives up
 };
 size_t local_solve_smem(int prec, int max_nb);
 void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
+// Block-envelope factor + inverse diagonal tiles (FP64) -> solve storage (prec 0/1/2);
+// tsc receives one scale per 32x32 tile for BF16.
+void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,
+                            void* dst, float* tsc, cudaStream_t st);
 
 // ---- eigen setup (k_lanczos.cu) ----------------------------------------------------
 struct EigArgs {

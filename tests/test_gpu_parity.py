@@ -40,7 +40,11 @@ class Case:
         return L.Solver(self.m, self.n, self.rp, self.c, self.v, self.part, self.N, **opts)
 
     def oracle(self, coarse=True):
-        return O.build_two_level(self.A, self.part, self.N, tau=self.tau, nev_max=self.nev, coarse=coarse)
+        key = (coarse, self.N, self.tau)
+        if self._M is None or self._M[0] != key:
+            self._M = (key, O.build_two_level(self.A, self.part, self.N, tau=self.tau, nev_max=self.nev,
+                                              coarse=coarse))
+        return self._M[1]
 
 
 def _tiny():
