@@ -97,6 +97,8 @@ typedef struct {
     double ms_coarse;        /* with time_kernels: total ms of the coarse GEMV launches      */
     int local_launches;      /* local-solve launches of the last solve                      */
     int launches;            /* kernels launched by the last solve (all of this library's)  */
+    double ms_iter;          /* with time_kernels: total ms of whole CG iterations (kernels) */
+    int lanes_csr, lanes_csc;/* lanes per row of A / per column of A^T chosen by the tuner  */
 } ls_info;
 
 typedef struct ls_handle ls_handle;

@@ -36,7 +36,8 @@ class ls_info(ctypes.Structure):
                 ("delta", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_eig", ctypes.c_double),
                 ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int),
                 ("ms_local", ctypes.c_double), ("ms_spmv", ctypes.c_double), ("ms_coarse", ctypes.c_double),
-                ("local_launches", ctypes.c_int), ("launches", ctypes.c_int)]
+                ("local_launches", ctypes.c_int), ("launches", ctypes.c_int), ("ms_iter", ctypes.c_double),
+                ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -120,7 +120,7 @@ struct ls_handle {
   bool own_stream = false;
   ls_options opt{};
   int64_t m = 0, n = 0, nnz = 0;
-  int N = 0, P = 0, lanes_csr = 8, lanes_csc = 32, prec = 0;
+  int N = 0, lanes_csr = 8, lanes_csc = 32, grid_csr = 0, grid_csc = 0, prec = 0;
 
   DevBuf<int64_t> row_ptr, col_ptr;
   DevBuf<int32_t> col, crow, part;
@@ -142,7 +142,8 @@ struct ls_handle {
   DevBuf<double> Z, Xinv;
 
   DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
-  DevBuf<double> part_pw, part_rz, part_rzo, part_rr, scal, ahist, bhist, sumout;
+  DevBuf<double> parts, scal, ahist, bhist;
+  DevBuf<unsigned> counters;  // ticket counters of the fused reductions
   DevBuf<int> ctr;
   double* pin = nullptr;  // pinned copy of the scalar slots
   int hist_cap = 0;
@@ -171,6 +172,10 @@ namespace {
 
 lsq::CsrDev csr(const ls_handle* h) { return lsq::CsrDev{h->m, h->n, h->row_ptr.p, h->col.p, h->val.p}; }
 lsq::CscDev csc(const ls_handle* h) { return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p}; }
+
+lsq::DotSite site(ls_handle* h, int slot, int counter, int out2 = 0) {
+  return lsq::DotSite{h->parts.p, lsq::kMaxGrid, h->counters.p + counter, h->scal.p + slot, out2};
+}
 
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -206,7 +211,7 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
   s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
   s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p;
   s.r = rin; s.r_old = flex ? h->r_old.p : nullptr; s.z = zout;
-  s.part_rz = dots ? h->part_rz.p : nullptr; s.part_rzo = flex ? h->part_rzo.p : nullptr; s.P = h->P;
+  s.dots = dots ? site(h, lsq::S_RZ, 2, lsq::S_RZO - lsq::S_RZ) : lsq::DotSite{};
   s.add_coarse_only = which == 2 ? 1 : 0;
   lsq::launch_scatter(s, st);
 }
@@ -219,21 +224,21 @@ void iteration(ls_handle* h, bool flex) {
   cudaStream_t st = h->st;
   const bool timed = h->opt.time_kernels != 0;
   if (timed) CK(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
-  lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, st);
-  lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, h->part_pw.p, h->P, h->lanes_csc, st);
+  lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, h->grid_csr, st);
+  lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, site(h, lsq::S_PW, 0), h->lanes_csc, h->grid_csc, st);
   if (timed) CK(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
-  lsq::launch_cg_update(h->n, h->P, h->part_pw.p, h->part_rz.p, h->p.p, h->w.p, h->x.p, h->r.p,
-                        flex ? h->r_old.p : nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->ahist.p, h->hist_cap, st);
+  lsq::launch_cg_update(h->n, h->scal.p, h->p.p, h->w.p, h->x.p, h->r.p, flex ? h->r_old.p : nullptr,
+                        site(h, lsq::S_RR, 1), h->ctr.p, h->ahist.p, h->hist_cap, st);
   precond(h, h->r.p, h->z.p, 0, true, flex, timed);
-  lsq::launch_p_update(h->n, h->P, h->part_rz.p, flex ? h->part_rzo.p : nullptr, h->part_rr.p, h->scal.p,
-                       h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, st);
+  lsq::launch_p_update(h->n, h->scal.p, h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, flex ? 1 : 0, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[5], st, cudaEventRecordExternal));
   CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
 }
 
-double dev_sum(ls_handle* h) {
-  lsq::launch_finish_sum(h->part_rr.p, h->P, h->sumout.p, h->st);
+// Reads one scalar slot of the device CG state (synchronising the stream).
+double dev_sum(ls_handle* h, int slot = lsq::S_TMP) {
   double v = 0;
-  CK(cudaMemcpyAsync(&v, h->sumout.p, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&v, h->scal.p + slot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return v;
 }
@@ -242,16 +247,16 @@ double dev_sum(ls_handle* h) {
 // Leaves the residual vector in h->w; adds the kernels it launched to *launches.
 double true_residual(ls_handle* h, int mode, int* launches) {
   cudaStream_t st = h->st;
-  lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, st);
+  lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, h->grid_csr, st);
   if (mode == 0) {
     lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);
-    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
-    *launches += 4;
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, site(h, lsq::S_TMP, 0), h->lanes_csc, h->grid_csc, st);
+    *launches += 3;
   } else {
-    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, st);
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, st);
     lsq::launch_axpby(h->n, 1.0, h->tv.p, -1.0, h->w.p, h->w.p, st);
-    lsq::launch_dot(h->n, h->w.p, h->w.p, h->part_rr.p, h->P, st);
-    *launches += 5;
+    lsq::launch_dot(h->n, h->w.p, h->w.p, site(h, lsq::S_TMP, 3), st);
+    *launches += 4;
   }
   return dev_sum(h);
 }
@@ -268,13 +273,13 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   int launches = 0;
   // r = g, gg = ||g||^2
   if (mode == 0) {
-    lsq::launch_spmv_csc(csc(h), h->bv.p, h->r.p, nullptr, h->part_rr.p, h->P, h->lanes_csc, st);
+    lsq::launch_spmv_csc(csc(h), h->bv.p, h->r.p, nullptr, site(h, lsq::S_TMP, 0), h->lanes_csc, h->grid_csc, st);
   } else {
     CK(cudaMemcpyAsync(h->r.p, h->tv.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    lsq::launch_dot(n, h->r.p, h->r.p, h->part_rr.p, h->P, st);
+    lsq::launch_dot(n, h->r.p, h->r.p, site(h, lsq::S_TMP, 3), st);
   }
   const double gg = dev_sum(h);
-  launches += 2;
+  launches += 1;
   if (!std::isfinite(gg)) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
   const double gn = std::sqrt(gg);
   lsq::launch_fill(n, 0.0, h->x.p, st);
@@ -290,8 +295,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   }
   auto restart = [&]() {
     precond(h, h->r.p, h->z.p, 0, true, false);
-    lsq::launch_p_update(n, h->P, h->part_rz.p, nullptr, h->part_rr.p, h->scal.p, h->ctr.p, h->bhist.p,
-                         h->hist_cap, h->z.p, h->p.p, 1, st);
+    lsq::launch_p_update(n, h->scal.p, h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 1, 0, st);
     launches += iteration_launches(h) - 3;
     inf.local_launches += 1;
   };
@@ -337,6 +341,9 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
       inf.ms_spmv += a;
       inf.ms_local += b;
       inf.ms_coarse += c;
+      float d = 0.f;
+      CK(cudaEventElapsedTime(&d, h->ev[0], h->ev[5]));
+      inf.ms_iter += d;
     }
     rr = h->pin[lsq::S_RR];
     if (h->pin[lsq::S_ERR] != 0.0)
@@ -378,6 +385,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.bad_subdomain = -1; inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.launches = launches;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -413,6 +421,44 @@ std::vector<T> to_host(const T* src, size_t count) {
   return v;
 }
 
+// Lanes per row (A) and per column (A^T) of the two sparse products, picked by timing
+// every power of two on the actual matrix (three launches each, CUDA events).
+void autotune_spmv(ls_handle* h) {
+  cudaStream_t st = h->st;
+  DevBuf<double> xa, ya;
+  xa.alloc(std::max(h->m, h->n));
+  ya.alloc(std::max(h->m, h->n));
+  xa.zero(st);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch) {
+    launch();  // warm
+    CK(cudaEventRecord(e0, st));
+    for (int k = 0; k < 3; ++k) launch();
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  float best = 1e30f;
+  // candidates: -1, 0 = warp-stream kernels (16 / 32 rows per warp), 1..32 = lanes per row
+  const int cand[] = {-1, 0, 1, 2, 4, 8, 16, 32};
+  for (int lanes : cand) {
+    const float ms = time_it([&] { lsq::launch_spmv_csr(csr(h), xa.p, ya.p, lanes, 0, st); });
+    if (ms < best) { best = ms; h->lanes_csr = lanes; }
+  }
+  best = 1e30f;
+  for (int lanes : cand) {
+    const float ms = time_it([&] { lsq::launch_spmv_csc(csc(h), xa.p, ya.p, nullptr, lsq::DotSite{}, lanes, 0, st); });
+    if (ms < best) { best = ms; h->lanes_csc = lanes; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_launch("sparse-product autotuning");
+}
+
 void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, const double* val_in,
               const int32_t* part_in) {
   const double t_begin = now_s();
@@ -432,7 +478,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   const int N = h->N;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
-  h->P = std::max(1, std::min(4 * sms, 2048));
+  (void)sms;
   h->lanes_csr = pow2_lanes((double)nnz / (double)h->m);
   h->lanes_csc = pow2_lanes((double)nnz / (double)h->n);
 
@@ -448,6 +494,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     h->cval.upload(cv, st);
   }
   h->part.upload(hpart, st);
+  autotune_spmv(h);
 
   // local plan
   h->total_local = hs.om_off[N];
@@ -693,8 +740,9 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->r0.alloc(std::max<int64_t>(h->n0p, 1)); h->r0.zero(st);
   h->y0.alloc(std::max<int64_t>(h->n0p, 1)); h->y0.zero(st);
   h->tv.alloc(h->n); h->bv.alloc(h->m);
-  h->part_pw.alloc(h->P); h->part_rz.alloc(h->P); h->part_rzo.alloc(h->P); h->part_rr.alloc(h->P);
-  h->scal.alloc(lsq::S_NSLOT); h->sumout.alloc(1);
+  h->parts.alloc(2 * (size_t)lsq::kMaxGrid);
+  h->counters.alloc(8); h->counters.zero(st);
+  h->scal.alloc(lsq::S_NSLOT); h->scal.zero(st);
   h->hist_cap = std::max(h->opt.maxit, h->opt.fixed_iters) + 8;
   h->ahist.alloc(h->hist_cap); h->bhist.alloc(h->hist_cap);
   h->ctr.alloc(1);
@@ -798,13 +846,13 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
       ls_status s = solve_core(h, 1, rtol, info);
       if (s != LS_OK) last = s;
       CK(cudaMemcpyAsync(lam.p, h->x.p, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
-      lsq::launch_spmv_csr(csr(h), lam.p, mu.p, h->lanes_csr, st);  // mu = A lambda = grad_b
+      lsq::launch_spmv_csr(csr(h), lam.p, mu.p, h->lanes_csr, h->grid_csr, st);  // mu = A lambda = grad_b
       if (grad_b)
         CK(cudaMemcpyAsync(grad_b + (int64_t)k * h->m, mu.p, sizeof(double) * h->m, cudaMemcpyDefault, st));
       if (grad_vals) {
         CK(cudaMemcpyAsync(xk.p, x + (int64_t)k * h->n, sizeof(double) * h->n, cudaMemcpyDefault, st));
         CK(cudaMemcpyAsync(h->bv.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, st));
-        lsq::launch_spmv_csr(csr(h), xk.p, h->q.p, h->lanes_csr, st);
+        lsq::launch_spmv_csr(csr(h), xk.p, h->q.p, h->lanes_csr, h->grid_csr, st);
         lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);  // rho = b - A x
         DevBuf<double> gv;
         double* gdst = grad_vals;
@@ -846,7 +894,7 @@ ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int 
       lsq::ScatterArgs s{};
       s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
       s.coarse = (h->coarse && h->n0 > 0) ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
-      s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p; s.r = h->tv.p; s.z = h->w.p; s.P = h->P;
+      s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p; s.r = h->tv.p; s.z = h->w.p;
       s.add_coarse_only = 1;
       lsq::launch_scatter(s, h->st);
     } else {
@@ -864,8 +912,8 @@ ls_status ls_apply_normal(ls_handle* h, const double* p, double* w) {
     if (!h || !p || !w) throw LsError(LS_ERR_INVALID, "bad arguments");
     CK(cudaSetDevice(h->dev));
     CK(cudaMemcpyAsync(h->tv.p, p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
-    lsq::launch_spmv_csr(csr(h), h->tv.p, h->q.p, h->lanes_csr, h->st);
-    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, nullptr, h->P, h->lanes_csc, h->st);
+    lsq::launch_spmv_csr(csr(h), h->tv.p, h->q.p, h->lanes_csr, h->grid_csr, h->st);
+    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, h->st);
     CK(cudaMemcpyAsync(w, h->w.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     CK(cudaStreamSynchronize(h->st));
     check_launch("normal-equations product");

@@ -1,10 +1,11 @@
-// Sparse products with A and A^T, the CG vector updates with deterministic fused
-// reductions, the overlap scatter-add with coarse prolongation, the coarse GEMV and
-// the adjoint-gradient kernel.  All FP64.
+// Sparse products with A and A^T, the CG vector updates, the overlap scatter-add with
+// coarse prolongation, the coarse GEMV and the adjoint-gradient kernel.  All FP64.
 //
-// Reductions: every kernel that produces a dot product writes one partial sum per
-// block; the consumer re-reduces the P partials in a fixed order in every block, so
-// results do not depend on scheduling and CUDA-graph replays are bit-reproducible.
+// Reductions: a kernel that produces a dot product writes one partial sum per block;
+// the last block to finish (an atomic ticket after a memory fence, no waiting) sums
+// the partials in block order and stores the scalar into a slot of the device CG
+// state.  The result does not depend on scheduling, so CUDA-graph replays are
+// bit-reproducible, and consumers read one scalar.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,7 +18,39 @@ __device__ __forceinline__ unsigned seg_mask(int V) {
   return V == 32 ? 0xffffffffu : (((1u << V) - 1u) << (lane / V * V));
 }
 
-// y = A x, V lanes per row (rows of A are short: a few stored entries each).
+// Block partials -> last block sums them in order -> *out (and a second sum if two).
+__device__ __forceinline__ void finish_dots(double s1, double s2, bool two, const DotSite& d) {
+  __shared__ double red[kWarps];
+  __shared__ bool last;
+  const double b1 = block_sum(s1, red);
+  const double b2 = two ? block_sum(s2, red) : 0.0;
+  if (threadIdx.x == 0) {
+    d.parts[blockIdx.x] = b1;
+    if (two) d.parts[d.stride + blockIdx.x] = b2;
+    __threadfence();
+    const unsigned t = atomicAdd(d.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double a1 = 0.0, a2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+      a1 += ((volatile double*)d.parts)[k];
+      if (two) a2 += ((volatile double*)d.parts)[d.stride + k];
+    }
+    a1 = block_sum(a1, red);
+    if (two) a2 = block_sum(a2, red);
+    if (threadIdx.x == 0) {
+      d.out[0] = a1;
+      if (two) d.out[d.out2] = a2;
+      *d.counter = 0u;
+    }
+  }
+}
+
+// y = A x, V lanes per row.  Each lane group walks its row with stride V; rows of a
+// few entries use small V so more rows are in flight per warp.
 template <int V>
 __global__ void __launch_bounds__(kThreads) k_spmv_csr(CsrDev A, const double* __restrict__ x,
                                                        double* __restrict__ y) {
@@ -27,20 +60,20 @@ __global__ void __launch_bounds__(kThreads) k_spmv_csr(CsrDev A, const double* _
   const unsigned mask = seg_mask(V);
   for (int64_t r = gt / V; r < A.m; r += stride) {
     double acc = 0.0;
-    const int64_t e1 = A.row_ptr[r + 1];
-    for (int64_t e = A.row_ptr[r] + sub; e < e1; e += V) acc += __ldg(A.val + e) * __ldg(x + __ldg(A.col + e));
+    const int64_t e0 = __ldg(A.row_ptr + r), e1 = __ldg(A.row_ptr + r + 1);
+#pragma unroll 4
+    for (int64_t e = e0 + sub; e < e1; e += V) acc += __ldg(A.val + e) * __ldg(x + __ldg(A.col + e));
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
     if (sub == 0) y[r] = acc;
   }
 }
 
-// w = A^T q through the CSC copy; optional fused partial sums of d . w.
+// w = A^T q through the CSC copy; optionally d.w into the dot site (d = w if null).
 template <int V>
 __global__ void __launch_bounds__(kThreads) k_spmv_csc(CscDev At, const double* __restrict__ q,
                                                        double* __restrict__ w, const double* __restrict__ d,
-                                                       double* __restrict__ part) {
-  __shared__ double red[kWarps];
+                                                       DotSite ds) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int sub = threadIdx.x % V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x / V;
@@ -48,8 +81,9 @@ __global__ void __launch_bounds__(kThreads) k_spmv_csc(CscDev At, const double* 
   double dacc = 0.0;
   for (int64_t j = gt / V; j < At.n; j += stride) {
     double acc = 0.0;
-    const int64_t e1 = At.col_ptr[j + 1];
-    for (int64_t e = At.col_ptr[j] + sub; e < e1; e += V) acc += __ldg(At.val + e) * __ldg(q + __ldg(At.row + e));
+    const int64_t e0 = __ldg(At.col_ptr + j), e1 = __ldg(At.col_ptr + j + 1);
+#pragma unroll 4
+    for (int64_t e = e0 + sub; e < e1; e += V) acc += __ldg(At.val + e) * __ldg(q + __ldg(At.row + e));
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
     if (sub == 0) {
@@ -57,21 +91,68 @@ __global__ void __launch_bounds__(kThreads) k_spmv_csc(CscDev At, const double* 
       dacc += (d ? d[j] : acc) * acc;
     }
   }
-  if (part) {
-    const double s = block_sum(dacc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-  }
+  if (ds.parts) finish_dots(dacc, 0.0, false, ds);
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, int P, const double* __restrict__ part_pw,
-                                                        const double* __restrict__ part_rz,
-                                                        const double* __restrict__ p, const double* __restrict__ w,
-                                                        double* __restrict__ x, double* __restrict__ r,
-                                                        double* __restrict__ r_old, double* __restrict__ part_rr,
-                                                        double* scal, int* ctr, double* alpha_hist, int cap) {
-  __shared__ double red[kWarps];
-  const double pw = reduce_partials(part_pw, P, red);
-  const double rz = reduce_partials(part_rz, P, red);
+// Warp-stream product y = B x for a CSR matrix B (A itself, or A^T through the CSC copy):
+// each warp takes R consecutive rows, loads all their entries coalesced (lanes stride the
+// entry range, all loads independent), keeps the products in shared memory, then lane k
+// sums row k in storage order.  Row blocks whose entries exceed CAP fall back to one
+// warp per row.  Optional fused d . y as in k_spmv_csc.
+template <int R, int CAP>
+__global__ void __launch_bounds__(kThreads) k_spmv_stream(int64_t nrows, const int64_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ idx,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ x, double* __restrict__ y,
+                                                          const double* __restrict__ d, DotSite ds) {
+  __shared__ double prod[kWarps][CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* sm = prod[w];
+  double dacc = 0.0;
+  const int64_t nblk = (nrows + R - 1) / R;
+  for (int64_t rb = (int64_t)blockIdx.x * kWarps + w; rb < nblk; rb += (int64_t)gridDim.x * kWarps) {
+    const int64_t r0 = rb * R;
+    const int64_t r = r0 + lane;
+    const bool mine = lane < R && r < nrows;
+    const int64_t plo = __ldg(ptr + (mine ? r : min(r0 + R, nrows)));
+    const int64_t rend = min(r0 + R, nrows);
+    const int64_t e1 = __ldg(ptr + rend);
+    const int64_t e0 = __shfl_sync(0xffffffffu, plo, 0);
+    const int64_t phi = __shfl_down_sync(0xffffffffu, plo, 1);
+    const int64_t my_hi = (lane == R - 1 || r + 1 >= rend) ? e1 : phi;
+    if (e1 - e0 <= CAP) {
+#pragma unroll 4
+      for (int64_t e = e0 + lane; e < e1; e += 32) sm[e - e0] = __ldg(val + e) * __ldg(x + __ldg(idx + e));
+      __syncwarp();
+      if (mine) {
+        double s = 0.0;
+        for (int64_t e = plo; e < my_hi; ++e) s += sm[e - e0];
+        y[r] = s;
+        dacc += (d ? d[r] : s) * s;
+      }
+      __syncwarp();
+    } else {
+      for (int64_t rr = r0; rr < rend; ++rr) {
+        const int64_t a0 = __ldg(ptr + rr), a1 = __ldg(ptr + rr + 1);
+        double s = 0.0;
+        for (int64_t e = a0 + lane; e < a1; e += 32) s += __ldg(val + e) * __ldg(x + __ldg(idx + e));
+        s = warp_sum(s);
+        if (lane == 0) {
+          y[rr] = s;
+          dacc += (d ? d[rr] : s) * s;
+        }
+      }
+    }
+  }
+  if (ds.parts) finish_dots(dacc, 0.0, false, ds);
+}
+
+// alpha = rz / pw; x += alpha p; r_old = r; r -= alpha w; rr = r.r
+__global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* scal, const double* __restrict__ p,
+                                                        const double* __restrict__ w, double* __restrict__ x,
+                                                        double* __restrict__ r, double* __restrict__ r_old,
+                                                        DotSite rr, int* ctr, double* alpha_hist, int cap) {
+  const double rz = scal[S_RZ], pw = scal[S_PW];
   const double alpha = rz / pw;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     scal[S_RZOLD] = rz;
@@ -89,32 +170,23 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, int P, const 
     r[k] = rk;
     acc += rk * rk;
   }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) part_rr[blockIdx.x] = s;
+  finish_dots(acc, 0.0, false, rr);
 }
 
-__global__ void __launch_bounds__(kThreads) k_p_update(int64_t n, int P, const double* __restrict__ part_rz,
-                                                       const double* __restrict__ part_rzo,
-                                                       const double* __restrict__ part_rr, double* scal,
-                                                       int* ctr, double* beta_hist, int cap,
-                                                       const double* __restrict__ z, double* __restrict__ p,
-                                                       int init) {
-  __shared__ double red[kWarps];
+// beta = rz_new / rz_old (or (rz_new - rzo_new) / rz_old, flexible); p = z + beta p.
+__global__ void __launch_bounds__(kThreads) k_p_update(int64_t n, double* scal, int* ctr, double* beta_hist,
+                                                       int cap, const double* __restrict__ z, double* __restrict__ p,
+                                                       int init, int flex) {
   double beta = 0.0;
   if (!init) {
-    const double rz_new = reduce_partials(part_rz, P, red);
-    const double num = part_rzo ? rz_new - reduce_partials(part_rzo, P, red) : rz_new;
+    const double num = flex ? scal[S_RZ] - scal[S_RZO] : scal[S_RZ];
     beta = num / scal[S_RZOLD];
-  }
-  if (blockIdx.x == 0 && !init) {
-    const double rr = reduce_partials(part_rr, P, red);
-    if (threadIdx.x == 0) {
-      scal[S_RR] = rr;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
       scal[S_BETA] = beta;
       const int it = *ctr;
       if (it >= 0 && it < cap) beta_hist[it] = beta;
       *ctr = it + 1;
-      if (!isfinite(beta) || !isfinite(rr)) scal[S_FLAG] = 1.0;
+      if (!isfinite(beta)) scal[S_FLAG] = 1.0;
     }
   }
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -122,19 +194,11 @@ __global__ void __launch_bounds__(kThreads) k_p_update(int64_t n, int P, const d
 }
 
 __global__ void __launch_bounds__(kThreads) k_dot(int64_t n, const double* __restrict__ a,
-                                                  const double* __restrict__ b, double* __restrict__ part) {
-  __shared__ double red[kWarps];
+                                                  const double* __restrict__ b, DotSite ds) {
   double acc = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     acc += a[k] * b[k];
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(kThreads) k_finish_sum(const double* __restrict__ part, int P, double* out) {
-  __shared__ double red[kWarps];
-  const double s = reduce_partials(part, P, red);
-  if (threadIdx.x == 0) *out = s;
+  finish_dots(acc, 0.0, false, ds);
 }
 
 __global__ void k_axpby(int64_t n, double alpha, const double* __restrict__ a, double beta,
@@ -151,7 +215,6 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ out) {
 // z_j = sum over the copies of column j in the subdomains (ascending subdomain order)
 //     + sum_t Zbar_{part[j]}[t, jj(j)] y0[coff + t]          (coarse prolongation)
 __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
-  __shared__ double red[kWarps];
   double acc_rz = 0.0, acc_rzo = 0.0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x) {
     double z = 0.0;
@@ -166,19 +229,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
       for (int t = 0; t < k; ++t) z += Zi[t * nIi] * a.y0[c0 + t];
     }
     a.z[j] = z;
-    if (a.part_rz) {
+    if (a.dots.parts) {
       acc_rz += a.r[j] * z;
       if (a.r_old) acc_rzo += a.r_old[j] * z;
     }
   }
-  if (a.part_rz) {
-    const double s = block_sum(acc_rz, red);
-    if (threadIdx.x == 0) a.part_rz[blockIdx.x] = s;
-    if (a.r_old) {
-      const double s2 = block_sum(acc_rzo, red);
-      if (threadIdx.x == 0) a.part_rzo[blockIdx.x] = s2;
-    }
-  }
+  if (a.dots.parts) finish_dots(acc_rz, acc_rzo, a.r_old != nullptr, a.dots);
 }
 
 // y0 = X r0 for the dense n0 x n0 coarse inverse (one warp per row).
@@ -221,8 +277,15 @@ int grid_for(int64_t work, int per_block, int cap) {
 
 }  // namespace
 
-void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, cudaStream_t st) {
-  const int grid = grid_for(A.m * lanes, kThreads, 1 << 16);
+void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int grid, cudaStream_t st) {
+  if (lanes <= 0) {
+    const int R = lanes == 0 ? 32 : 16;
+    if (grid <= 0) grid = grid_for((A.m + R - 1) / R, kWarps, kMaxGrid);
+    if (lanes == 0) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(A.m, A.row_ptr, A.col, A.val, x, y, nullptr, DotSite{});
+    else k_spmv_stream<16, 768><<<grid, kThreads, 0, st>>>(A.m, A.row_ptr, A.col, A.val, x, y, nullptr, DotSite{});
+    return;
+  }
+  if (grid <= 0) grid = grid_for(A.m * lanes, kThreads, kMaxGrid);
   switch (lanes) {
     case 1: k_spmv_csr<1><<<grid, kThreads, 0, st>>>(A, x, y); break;
     case 2: k_spmv_csr<2><<<grid, kThreads, 0, st>>>(A, x, y); break;
@@ -233,53 +296,53 @@ void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, cud
   }
 }
 
-void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, double* part,
-                     int P, int lanes, cudaStream_t st) {
-  // With partials the grid is exactly P blocks (the consumer reduces P entries).
-  const int grid = part ? P : grid_for(At.n * lanes, kThreads, 1 << 16);
+void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, const DotSite& ds, int lanes,
+                     int grid, cudaStream_t st) {
+  if (lanes <= 0) {
+    const int R = lanes == 0 ? 32 : 16;
+    if (grid <= 0) grid = grid_for((At.n + R - 1) / R, kWarps, kMaxGrid);
+    if (lanes == 0) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(At.n, At.col_ptr, At.row, At.val, q, w, d, ds);
+    else k_spmv_stream<16, 768><<<grid, kThreads, 0, st>>>(At.n, At.col_ptr, At.row, At.val, q, w, d, ds);
+    return;
+  }
+  if (grid <= 0) grid = grid_for(At.n * lanes, kThreads, kMaxGrid);
   switch (lanes) {
-    case 1: k_spmv_csc<1><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
-    case 2: k_spmv_csc<2><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
-    case 4: k_spmv_csc<4><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
-    case 8: k_spmv_csc<8><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
-    case 16: k_spmv_csc<16><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
-    default: k_spmv_csc<32><<<grid, kThreads, 0, st>>>(At, q, w, d, part); break;
+    case 1: k_spmv_csc<1><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
+    case 2: k_spmv_csc<2><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
+    case 4: k_spmv_csc<4><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
+    case 8: k_spmv_csc<8><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
+    case 16: k_spmv_csc<16><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
+    default: k_spmv_csc<32><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
   }
 }
 
-void launch_cg_update(int64_t n, int P, const double* part_pw, const double* part_rz, const double* p,
-                      const double* w, double* x, double* r, double* r_old, double* part_rr,
-                      double* scal, int* ctr, double* alpha_hist, int hist_cap, cudaStream_t st) {
-  k_cg_update<<<P, kThreads, 0, st>>>(n, P, part_pw, part_rz, p, w, x, r, r_old, part_rr, scal, ctr,
-                                      alpha_hist, hist_cap);
+void launch_cg_update(int64_t n, double* scal, const double* p, const double* w, double* x, double* r, double* r_old,
+                      const DotSite& rr, int* ctr, double* alpha_hist, int hist_cap, cudaStream_t st) {
+  k_cg_update<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, scal, p, w, x, r, r_old, rr, ctr, alpha_hist,
+                                                                    hist_cap);
 }
 
-void launch_p_update(int64_t n, int P, const double* part_rz, const double* part_rzo,
-                     const double* part_rr, double* scal, int* ctr, double* beta_hist, int hist_cap,
-                     const double* z, double* p, int init, cudaStream_t st) {
-  k_p_update<<<P, kThreads, 0, st>>>(n, P, part_rz, part_rzo, part_rr, scal, ctr, beta_hist, hist_cap, z,
-                                     p, init);
+void launch_p_update(int64_t n, double* scal, int* ctr, double* beta_hist, int hist_cap, const double* z, double* p,
+                     int init, int flex, cudaStream_t st) {
+  k_p_update<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, scal, ctr, beta_hist, hist_cap, z, p, init,
+                                                                   flex);
 }
 
-void launch_dot(int64_t n, const double* a, const double* b, double* part, int P, cudaStream_t st) {
-  k_dot<<<P, kThreads, 0, st>>>(n, a, b, part);
-}
-
-void launch_finish_sum(const double* part, int P, double* out, cudaStream_t st) {
-  k_finish_sum<<<1, kThreads, 0, st>>>(part, P, out);
+void launch_dot(int64_t n, const double* a, const double* b, const DotSite& ds, cudaStream_t st) {
+  k_dot<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, a, b, ds);
 }
 
 void launch_axpby(int64_t n, double alpha, const double* a, double beta, const double* b, double* out,
                   cudaStream_t st) {
-  k_axpby<<<grid_for(n, kThreads, 4096), kThreads, 0, st>>>(n, alpha, a, beta, b, out);
+  k_axpby<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, alpha, a, beta, b, out);
 }
 
 void launch_fill(int64_t n, double v, double* out, cudaStream_t st) {
-  k_fill<<<grid_for(n, kThreads, 4096), kThreads, 0, st>>>(n, v, out);
+  k_fill<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, v, out);
 }
 
 void launch_scatter(const ScatterArgs& a, cudaStream_t st) {
-  k_scatter<<<a.P, kThreads, 0, st>>>(a);
+  k_scatter<<<grid_for(a.n, kThreads, kVecGrid), kThreads, 0, st>>>(a);
 }
 
 void launch_gemv(int64_t n0, const double* X, const double* r0, double* y0, cudaStream_t st) {

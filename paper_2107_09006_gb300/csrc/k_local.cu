@@ -90,6 +90,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   constexpr int ES = sizeof(TF);
   constexpr int CC = kStageBytes / (kT * ES);  // columns per stage
   constexpr int CHUNK = CC * kT;                // elements per stage
+  constexpr int G = kThreads / CC;              // row groups of the backward panel update
+  constexpr int RG = kT / G;                    // rows per group
+  constexpr bool kSplit = (ES == 8);            // spread the 32x32 products over the warps
+  static_assert(G * CC == kThreads && G * RG == kT, "stage geometry");
   TF* ring = reinterpret_cast<TF*>(smem_raw);
   TA* red = reinterpret_cast<TA*>(smem_raw + S * kStageBytes);
   TA* tv = red + kWarps * 32;
@@ -185,50 +189,99 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
       if (cons.k == 0) {
         red[w * 32 + lane] = acc;
         __syncthreads();
+        const TF* D = ch + (offw - lo) * kT;  // inverse tile, column-major
+        const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
         if (w == 0) {
           TA s = 0;
 #pragma unroll
           for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
           tv[lane] = v[b * kT + lane] - s;
           __syncwarp();
-          const TF* D = ch + (offw - lo) * kT;  // inverse tile, column-major
-          const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
-          TA x = 0;
+          if (!kSplit) {
+            TA x = 0;
 #pragma unroll 8
-          for (int c = 0; c < kT; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
-          v[b * kT + lane] = x * dsc;
+            for (int c = 0; c < kT; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
+            v[b * kT + lane] = x * dsc;
+          }
+        }
+        if (kSplit) {  // FP64: the 32x32 product spread over the warps (the FP64 pipe is narrow)
+          __syncthreads();
+          TA x = 0;
+#pragma unroll
+          for (int c = 4 * w; c < 4 * w + 4; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
+          red[w * 32 + lane] = x;
+          __syncthreads();
+          if (w == 0) {
+            TA s = 0;
+#pragma unroll
+            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+            v[b * kT + lane] = s * dsc;
+          }
         }
       }
     } else {
       if (cons.k == 0) {
-        if (w == 0) {
-          tv[lane] = v[b * kT + lane];
-          __syncwarp();
-          const TF* D = ch + (offw - lo) * kT;
-          const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
-          TA x = 0;
+        const TF* D = ch + (offw - lo) * kT;
+        const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
+        if (w == 0) tv[lane] = v[b * kT + lane];
+        __syncthreads();
+        if (!kSplit) {
+          if (w == 0) {
+            TA x = 0;
 #pragma unroll 8
-          for (int u = 0; u < kT; ++u) {
-            const int r = (u + lane) & 31;  // skewed walk: no bank conflicts
+            for (int u = 0; u < kT; ++u) {
+              const int r = (u + lane) & 31;  // skewed walk: no bank conflicts
+              x += Val<TF>::f(D[lane * kT + r]) * tv[r];
+            }
+            x *= dsc;
+            xv[lane] = x;
+            v[b * kT + lane] = x;
+          }
+        } else {
+          TA x = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * w + ((u + lane) & 3);
             x += Val<TF>::f(D[lane * kT + r]) * tv[r];
           }
-          x *= dsc;
-          xv[lane] = x;
-          v[b * kT + lane] = x;
+          red[w * 32 + lane] = x;
+          __syncthreads();
+          if (w == 0) {
+            TA s = 0;
+#pragma unroll
+            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+            s *= dsc;
+            xv[lane] = s;
+            v[b * kT + lane] = s;
+          }
         }
         __syncthreads();
       }
+      // v_window -= L_off^T x_b: thread (column c, row group g) sums rows of its group
       TA* vw = v + t0 * kT;
-      for (int c = lo + tid; c < phi; c += blockDim.x) {
-        const TF* col = ch + (c - lo) * kT;
-        TA s = 0;
+      const int cl = tid % CC, g = tid / CC;
+      const int c = lo + cl;
+      TA s = 0;
+      if (c < phi) {
+        const TF* col = ch + cl * kT + g * RG;
 #pragma unroll 8
-        for (int u = 0; u < kT; ++u) {
-          const int r = (u + c) & 31;
-          s += Val<TF>::f(col[r]) * xv[r];
+        for (int u = 0; u < RG; ++u) {
+          const int r = (u + c) & (RG - 1);
+          s += Val<TF>::f(col[r]) * xv[g * RG + r];
         }
         if (sc) s *= (TA)sc[c >> 5];
-        vw[c] -= s;
+      }
+      if (G == 1) {
+        if (c < phi) vw[c] -= s;
+      } else {
+        red[g * CC + cl] = s;
+        __syncthreads();
+        if (g == 0 && c < phi) {
+          TA t = 0;
+#pragma unroll
+          for (int u = 0; u < G; ++u) t += red[u * CC + cl];
+          vw[c] -= t;
+        }
       }
     }
     __syncthreads();
@@ -322,16 +375,18 @@ void launch_impl(int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
 
 }  // namespace
 
+// Stages per precision: as deep a ring as two CTAs per SM allow (228 KB per SM) for
+// subdomains of up to 181 block rows.
 size_t local_solve_smem(int prec, int max_nb) {
   if (prec == 0) return smem_bytes<double, double, 3>(max_nb);
-  if (prec == 1) return smem_bytes<float, float, 4>(max_nb);
-  return smem_bytes<__nv_bfloat16, float, 4>(max_nb);
+  if (prec == 1) return smem_bytes<float, float, 5>(max_nb);
+  return smem_bytes<__nv_bfloat16, float, 5>(max_nb);
 }
 
 void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
   if (prec == 0) launch_impl<double, double, 3>(N, max_nb, a, st);
-  else if (prec == 1) launch_impl<float, float, 4>(N, max_nb, a, st);
-  else launch_impl<__nv_bfloat16, float, 4>(N, max_nb, a, st);
+  else if (prec == 1) launch_impl<float, float, 5>(N, max_nb, a, st);
+  else launch_impl<__nv_bfloat16, float, 5>(N, max_nb, a, st);
 }
 
 void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,

@@ -10,21 +10,31 @@ namespace lsq {
 struct CsrDev { int64_t m, n; const int64_t* row_ptr; const int32_t* col; const double* val; };
 struct CscDev { int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val; };
 
-// Scalar slots of the CG state kept on the device.
-enum { S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_ERR = 6, S_NSLOT = 8 };
+// Scalar slots of the CG state kept on the device (copied to the host each iteration).
+enum {
+  S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_ERR = 6,
+  S_PW = 7, S_RZ = 8, S_RZO = 9, S_TMP = 10, S_NSLOT = 12
+};
+constexpr int kMaxGrid = 65536;  // largest grid of a kernel that produces a dot product
+constexpr int kVecGrid = 1216;   // grid cap of the n-vector kernels (8 blocks of 256 per SM)
 
-void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, cudaStream_t st);
-// w = A^T q; if part != nullptr also writes per-block partial sums of d.w (d = w if d == nullptr).
-void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, double* part,
-                     int P, int lanes, cudaStream_t st);
-void launch_cg_update(int64_t n, int P, const double* part_pw, const double* part_rz, const double* p,
-                      const double* w, double* x, double* r, double* r_old, double* part_rr,
-                      double* scal, int* ctr, double* alpha_hist, int hist_cap, cudaStream_t st);
-void launch_p_update(int64_t n, int P, const double* part_rz, const double* part_rzo,
-                     const double* part_rr, double* scal, int* ctr, double* beta_hist, int hist_cap,
-                     const double* z, double* p, int init, cudaStream_t st);
-void launch_dot(int64_t n, const double* a, const double* b, double* part, int P, cudaStream_t st);
-void launch_finish_sum(const double* part, int P, double* out, cudaStream_t st);
+// Where a fused dot product goes: per-block partials (parts[block], second sum at
+// parts[stride + block]), a ticket counter (zero between uses) and the output slot(s)
+// out[0] and out[out2].
+struct DotSite { double* parts; int stride; unsigned* counter; double* out; int out2; };
+
+void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int grid, cudaStream_t st);
+// w = A^T q; with ds.parts != nullptr also (d . w) -> *ds.out (d = w if d == nullptr).
+void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, const DotSite& ds, int lanes,
+                     int grid, cudaStream_t st);
+// alpha = scal[S_RZ] / scal[S_PW]; x += alpha p; r_old = r (if given); r -= alpha w; r.r -> rr.
+void launch_cg_update(int64_t n, double* scal, const double* p, const double* w, double* x, double* r,
+                      double* r_old, const DotSite& rr, int* ctr, double* alpha_hist, int hist_cap,
+                      cudaStream_t st);
+// beta from the scalar slots (plain or flexible form), p = z + beta p (init: p = z).
+void launch_p_update(int64_t n, double* scal, int* ctr, double* beta_hist, int hist_cap, const double* z, double* p,
+                     int init, int flex, cudaStream_t st);
+void launch_dot(int64_t n, const double* a, const double* b, const DotSite& ds, cudaStream_t st);
 void launch_axpby(int64_t n, double alpha, const double* a, double beta, const double* b, double* out,
                   cudaStream_t st);
 void launch_fill(int64_t n, double v, double* out, cudaStream_t st);
@@ -36,7 +46,8 @@ struct ScatterArgs {
   int coarse; const int32_t* part; const int32_t* jj_of; const int64_t* zoff; const int32_t* coff;
   const int32_t* nI; const double* Z; const double* y0;
   const double* r; const double* r_old;  // for the fused dots (r_old may be null)
-  double* z; double* part_rz; double* part_rzo; int P;
+  double* z;
+  DotSite dots;  // r.z -> out[0], r_old.z -> out[out2]; parts == nullptr: no dots
   int add_coarse_only;  // 1: z = coarse term only; 2: z = local sum only
 };
 void launch_scatter(const ScatterArgs& a, cudaStream_t st);
