@@ -67,6 +67,8 @@ def _load():
         "ls_apply_normal": (ctypes.c_int, [vp, vp, vp]),
         "ls_query": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, i64]),
         "ls_build_index_sets": (ctypes.c_int, [i64, i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ls_normal_product_noalloc": (ctypes.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]),
+        "ls_noalloc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -78,7 +80,8 @@ def _load():
 _lib = _load()
 LIBRARY_PATH = _LIB_PATH
 EXPORTED = ("ls_default_options", "ls_setup", "ls_solve", "ls_backward", "ls_free", "ls_last_error",
-            "ls_handle_info", "ls_apply_preconditioner", "ls_apply_normal", "ls_query", "ls_build_index_sets")
+            "ls_handle_info", "ls_apply_preconditioner", "ls_apply_normal", "ls_query", "ls_build_index_sets",
+            "ls_normal_product_noalloc", "ls_noalloc_last_error")
 
 
 def _ptr(a) -> int | None:
@@ -164,6 +167,15 @@ def ls_apply_normal(h, p, w):
 def ls_query(h, kind, i, out):
     _check(_lib.ls_query(h, int(kind), int(i), _ptr(out), int(out.size if isinstance(out, np.ndarray) else out.numel())))
     return out
+
+
+def ls_normal_product_noalloc(m, n, row_ptr, col, val, col_ptr, row, cval, nnz, p, w, stream=None):
+    """w = A^T (A p) with no allocation by the library (device arrays in, device w out);
+    asynchronous on ``stream`` (a raw cudaStream_t handle or None)."""
+    st = _lib.ls_normal_product_noalloc(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(col_ptr),
+                                        _ptr(row), _ptr(cval), int(nnz), _ptr(p), _ptr(w), stream)
+    if st != LS_OK:
+        raise LSError(st, _lib.ls_noalloc_last_error().decode())
 
 
 def ls_build_index_sets(m, n, row_ptr, col, nparts, part):
