@@ -125,6 +125,10 @@ struct ls_handle {
   DevBuf<int64_t> row_ptr, col_ptr;
   DevBuf<int32_t> col, crow, part;
   DevBuf<double> val, cval;
+  lsq::SellDev sellA{}, sellB{};  // sliced-ELL copies of A and A^T (pointers below)
+  DevBuf<int64_t> sellA_off, sellB_off;
+  DevBuf<int32_t> sellA_perm, sellA_col, sellB_perm, sellB_col;
+  DevBuf<double> sellA_val, sellB_val;
 
   DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
   DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
@@ -170,8 +174,14 @@ struct ls_handle {
 
 namespace {
 
-lsq::CsrDev csr(const ls_handle* h) { return lsq::CsrDev{h->m, h->n, h->row_ptr.p, h->col.p, h->val.p}; }
-lsq::CscDev csc(const ls_handle* h) { return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p}; }
+lsq::CsrDev csr(const ls_handle* h) {
+  return lsq::CsrDev{h->m, h->n, h->row_ptr.p, h->col.p, h->val.p,
+                     lsq::SellDev{h->sellA.nslices, h->sellA_off.p, h->sellA_perm.p, h->sellA_col.p, h->sellA_val.p}};
+}
+lsq::CscDev csc(const ls_handle* h) {
+  return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p,
+                     lsq::SellDev{h->sellB.nslices, h->sellB_off.p, h->sellB_perm.p, h->sellB_col.p, h->sellB_val.p}};
+}
 
 lsq::DotSite site(ls_handle* h, int slot, int counter, int out2 = 0) {
   return lsq::DotSite{h->parts.p, lsq::kMaxGrid, h->counters.p + counter, h->scal.p + slot, out2};
@@ -443,8 +453,8 @@ void autotune_spmv(ls_handle* h) {
     return ms;
   };
   float best = 1e30f;
-  // candidates: -1, 0 = warp-stream kernels (16 / 32 rows per warp), 1..32 = lanes per row
-  const int cand[] = {-1, 0, 1, 2, 4, 8, 16, 32};
+  // candidates: -2 sliced ELL, -1 / 0 warp-stream (16 / 32 rows per warp), 1..32 lanes per row
+  const int cand[] = {-2, -1, 0, 1, 2, 4, 8, 16, 32};
   for (int lanes : cand) {
     const float ms = time_it([&] { lsq::launch_spmv_csr(csr(h), xa.p, ya.p, lanes, 0, st); });
     if (ms < best) { best = ms; h->lanes_csr = lanes; }
@@ -492,6 +502,17 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     std::vector<double> cv(nnz);
     for (int64_t s = 0; s < nnz; ++s) cv[s] = hval[hs.csc_perm[s]];
     h->cval.upload(cv, st);
+    // sliced-ELL copies of A and A^T (candidates of the product autotuner)
+    lsq::SellHost sa, sb;
+    lsq::build_sell(h->m, hrp.data(), hcol.data(), hval.data(), 256, sa);
+    lsq::build_sell(h->n, hs.csc_ptr.data(), hs.csc_row.data(), cv.data(), 256, sb);
+    h->sellA.nslices = sa.nslices;
+    h->sellA_off.upload(sa.off, st); h->sellA_perm.upload(sa.perm, st);
+    h->sellA_col.upload(sa.col, st); h->sellA_val.upload(sa.val, st);
+    h->sellB.nslices = sb.nslices;
+    h->sellB_off.upload(sb.off, st); h->sellB_perm.upload(sb.perm, st);
+    h->sellB_col.upload(sb.col, st); h->sellB_val.upload(sb.val, st);
+    CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   }
   h->part.upload(hpart, st);
   autotune_spmv(h);

@@ -40,6 +40,45 @@ void parallel_for(int count, F&& f) {
 
 }  // namespace
 
+void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const double* val, int window,
+                SellHost& out) {
+  out = SellHost();
+  const int64_t ns = (nrows + 31) / 32;
+  out.nslices = ns;
+  out.perm.assign(ns * 32, -1);
+  std::vector<int32_t> order(nrows);
+  for (int64_t r = 0; r < nrows; ++r) order[r] = (int32_t)r;
+  for (int64_t w0 = 0; w0 < nrows; w0 += window) {
+    const int64_t w1 = std::min(nrows, w0 + window);
+    std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int32_t a, int32_t b) {
+      return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
+    });
+  }
+  out.off.assign(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t wmax = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t k = s * 32 + l;
+      if (k < nrows) {
+        out.perm[k] = order[k];
+        wmax = std::max(wmax, ptr[order[k] + 1] - ptr[order[k]]);
+      }
+    }
+    out.off[s + 1] = out.off[s] + 32 * wmax;
+  }
+  out.col.assign(out.off[ns], 0);
+  out.val.assign(out.off[ns], 0.0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = out.perm[s * 32 + l];
+      if (r < 0) continue;
+      for (int64_t e = ptr[r], k = 0; e < ptr[r + 1]; ++e, ++k) {
+        out.col[out.off[s] + 32 * k + l] = idx[e];
+        out.val[out.off[s] + 32 * k + l] = val[e];
+      }
+    }
+}
+
 std::string build_host_sets(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
                             int N, const int32_t* part, bool with_pairs, HostSets& hs) {
   if (m < 1 || n < 1) return "m and n must be positive";

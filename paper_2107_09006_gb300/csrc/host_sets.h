@@ -61,6 +61,18 @@ struct HostSets {
   std::vector<int32_t> pair_pi, pair_pj;
 };
 
+// Sliced-ELL copy of a CSR matrix: slices of 32 rows, rows ordered by decreasing length
+// inside windows of `window` rows (stable), entries column-major inside a slice, zero
+// padding with column 0; perm maps slice rows to matrix rows (-1 for padding rows).
+struct SellHost {
+  int64_t nslices = 0;
+  std::vector<int64_t> off;
+  std::vector<int32_t> perm, col;
+  std::vector<double> val;
+};
+void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const double* val, int window,
+                SellHost& out);
+
 // Validates the CSR pattern and the partition and fills hs.  Returns an empty
 // string on success, else the reason the input is invalid.  col must be strictly
 // increasing within each row; part[j] must lie in [0, N).

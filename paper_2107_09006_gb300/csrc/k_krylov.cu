@@ -147,6 +147,32 @@ __global__ void __launch_bounds__(kThreads) k_spmv_stream(int64_t nrows, const i
   if (ds.parts) finish_dots(dacc, 0.0, false, ds);
 }
 
+// Sliced-ELL product: one warp per slice of 32 rows, lane l owns slice row l; every
+// step k loads 32 consecutive (column, value) pairs, so there is no per-row pointer
+// chase and the gathers of successive k are independent.
+__global__ void __launch_bounds__(kThreads) k_spmv_sell(SellDev S, const double* __restrict__ x,
+                                                        double* __restrict__ y, const double* __restrict__ d,
+                                                        DotSite ds) {
+  const int lane = threadIdx.x & 31;
+  double dacc = 0.0;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S.nslices;
+       s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t o = __ldg(S.off + s);
+    const int W = (int)((__ldg(S.off + s + 1) - o) >> 5);
+    const int r = __ldg(S.perm + s * 32 + lane);
+    const int32_t* cp = S.col + o + lane;
+    const double* vp = S.val + o + lane;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < W; ++k) acc += __ldg(vp + 32 * k) * __ldg(x + __ldg(cp + 32 * k));
+    if (r >= 0) {
+      y[r] = acc;
+      dacc += (d ? d[r] : acc) * acc;
+    }
+  }
+  if (ds.parts) finish_dots(dacc, 0.0, false, ds);
+}
+
 // alpha = rz / pw; x += alpha p; r_old = r; r -= alpha w; rr = r.r
 __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* scal, const double* __restrict__ p,
                                                         const double* __restrict__ w, double* __restrict__ x,
@@ -278,6 +304,11 @@ int grid_for(int64_t work, int per_block, int cap) {
 }  // namespace
 
 void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int grid, cudaStream_t st) {
+  if (lanes == -2) {
+    if (grid <= 0) grid = grid_for(A.sell.nslices, kWarps, kMaxGrid);
+    k_spmv_sell<<<grid, kThreads, 0, st>>>(A.sell, x, y, nullptr, DotSite{});
+    return;
+  }
   if (lanes <= 0) {
     const int R = lanes == 0 ? 32 : 16;
     if (grid <= 0) grid = grid_for((A.m + R - 1) / R, kWarps, kMaxGrid);
@@ -298,6 +329,11 @@ void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int
 
 void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, const DotSite& ds, int lanes,
                      int grid, cudaStream_t st) {
+  if (lanes == -2) {
+    if (grid <= 0) grid = grid_for(At.sell.nslices, kWarps, kMaxGrid);
+    k_spmv_sell<<<grid, kThreads, 0, st>>>(At.sell, q, w, d, ds);
+    return;
+  }
   if (lanes <= 0) {
     const int R = lanes == 0 ? 32 : 16;
     if (grid <= 0) grid = grid_for((At.n + R - 1) / R, kWarps, kMaxGrid);

@@ -58,6 +58,13 @@ template <> struct Val<__nv_bfloat16> {
 constexpr int kStageBytes = 16384;
 constexpr long long kWaitCycles = 4000000000ll;  // about two seconds at GB300 clocks
 
+// Byte offset of the local vector v in shared memory: after the ring, the reduction
+// buffers and the barriers, rounded up to 16 bytes (vector reads of v).
+template <class TA, int S>
+__host__ __device__ constexpr size_t v_offset() {
+  return ((size_t)S * kStageBytes + (kWarps * 32 + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) + 15) / 16 * 16;
+}
+
 // Order of the chunks one CTA consumes: forward sweep, blocks ascending, each segment's
 // chunks from its start; backward sweep, blocks descending, each segment's chunks from
 // its end.  Chunk k of a segment (counted from its end) covers the columns
@@ -93,14 +100,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   constexpr int G = kThreads / CC;              // row groups of the backward panel update
   constexpr int RG = kT / G;                    // rows per group
   constexpr bool kSplit = (ES == 8);            // spread the 32x32 products over the warps
+  constexpr bool kVec = (sizeof(TA) == 4);      // FP32 arithmetic: vectorised inner loops
+  constexpr int CPW = CC / kWarps;              // forward: contiguous columns per warp
+  constexpr int XG = 16 / ES;                   // rows per 16-byte read of a column
   static_assert(G * CC == kThreads && G * RG == kT, "stage geometry");
+  static_assert(!kVec || (CPW % 4 == 0 && CC <= kThreads), "vectorised geometry");
   TF* ring = reinterpret_cast<TF*>(smem_raw);
   TA* red = reinterpret_cast<TA*>(smem_raw + S * kStageBytes);
   TA* tv = red + kWarps * 32;
   TA* xv = tv + 32;
   uint64_t* bars = reinterpret_cast<uint64_t*>(xv + 32);
   int* abort_flag = reinterpret_cast<int*>(bars + S);
-  TA* v = reinterpret_cast<TA*>(bars + S + 1);
+  TA* v = reinterpret_cast<TA*>(smem_raw + v_offset<TA, S>());  // 16-byte aligned
 
   const int i = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -155,6 +166,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
 
   cons.start(tf, nb, CC);
   TA acc = 0;
+  TA xr[kT];                                        // rotated copy of x_b (vectorised path)
+  const int rot = kVec ? (tid & (kT / XG - 1)) : 0;  // this thread's skew of 16-byte groups
   int q = 0;
   while (!cons.done()) {
     const int stage = q % S;
@@ -181,10 +194,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     if (cons.sweep == 0) {
       if (cons.k == cons.nchunks(b) - 1) acc = 0;
       TA* vw = v + t0 * kT;
-      for (int c = lo + w; c < phi; c += kWarps) {
-        TA p = Val<TF>::f(ch[(c - lo) * kT + lane]);
-        if (sc) p *= (TA)sc[c >> 5];
-        acc += p * vw[c];
+      if constexpr (kVec) {
+        // warp w takes the contiguous columns [c0, c0 + CPW) of the chunk (one BF16 tile)
+        const int c0 = lo + w * CPW;
+        if (c0 < phi) {
+          const TF* colp = ch + (c0 - lo) * kT + lane;
+          TA s0 = 0, s1 = 0;
+          if (c0 + CPW <= phi) {
+#pragma unroll
+            for (int j = 0; j < CPW; j += 4) {
+              const float4 v4 = *reinterpret_cast<const float4*>(vw + c0 + j);
+              s0 += Val<TF>::f(colp[(j + 0) * kT]) * v4.x;
+              s1 += Val<TF>::f(colp[(j + 1) * kT]) * v4.y;
+              s0 += Val<TF>::f(colp[(j + 2) * kT]) * v4.z;
+              s1 += Val<TF>::f(colp[(j + 3) * kT]) * v4.w;
+            }
+          } else {
+            for (int c = c0; c < phi; ++c) s0 += Val<TF>::f(colp[(c - c0) * kT]) * vw[c];
+          }
+          acc += sc ? (s0 + s1) * (TA)sc[c0 >> 5] : (s0 + s1);
+        }
+      } else {
+        for (int c = lo + w; c < phi; c += kWarps) {
+          TA p = Val<TF>::f(ch[(c - lo) * kT + lane]);
+          if (sc) p *= (TA)sc[c >> 5];
+          acc += p * vw[c];
+        }
       }
       if (cons.k == 0) {
         red[w * 32 + lane] = acc;
@@ -256,9 +291,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           }
         }
         __syncthreads();
+        if constexpr (kVec) {
+          // this thread's copy of x_b, rotated like its skewed column reads
+#pragma unroll
+          for (int k = 0; k < kT; ++k) xr[k] = xv[(((k / XG) + rot) & (kT / XG - 1)) * XG + (k % XG)];
+        }
       }
-      // v_window -= L_off^T x_b: thread (column c, row group g) sums rows of its group
+      // v_window -= L_off^T x_b
       TA* vw = v + t0 * kT;
+      if constexpr (kVec) {
+        // one thread per column; 16-byte reads walk the column in a rotated order
+        const int c = lo + tid;
+        if (tid < CC && c < phi) {
+          const TF* col = ch + (c - lo) * kT;
+          TA s = 0;
+          if constexpr (ES == 4) {
+            const float4* c4 = reinterpret_cast<const float4*>(col);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const float4 u = c4[(k + rot) & 7];
+              s += u.x * xr[4 * k] + u.y * xr[4 * k + 1] + u.z * xr[4 * k + 2] + u.w * xr[4 * k + 3];
+            }
+          } else {
+            const uint4* c8 = reinterpret_cast<const uint4*>(col);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint4 u = c8[(k + rot) & 3];
+              const uint32_t wds[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                s += __uint_as_float(wds[h] << 16) * xr[8 * k + 2 * h];
+                s += __uint_as_float(wds[h] & 0xffff0000u) * xr[8 * k + 2 * h + 1];
+              }
+            }
+          }
+          if (sc) s *= (TA)sc[c >> 5];
+          vw[c] -= s;
+        }
+      } else {
       const int cl = tid % CC, g = tid / CC;
       const int c = lo + cl;
       TA s = 0;
@@ -282,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           for (int u = 0; u < G; ++u) t += red[u * CC + cl];
           vw[c] -= t;
         }
+      }
       }
     }
     __syncthreads();
@@ -358,8 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_to_solve_layout<__nv_bfloat16>(con
 
 template <class TF, class TA, int S>
 size_t smem_bytes(int max_nb) {
-  return (size_t)S * kStageBytes + (kWarps * 32 + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) +
-         (size_t)max_nb * kT * sizeof(TA);
+  return v_offset<TA, S>() + (size_t)max_nb * kT * sizeof(TA);
 }
 
 template <class TF, class TA, int S>

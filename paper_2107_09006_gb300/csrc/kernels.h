@@ -7,8 +7,19 @@
 namespace lsq {
 
 // ---- sparse products and CG vector kernels (k_krylov.cu) ----------------------------
-struct CsrDev { int64_t m, n; const int64_t* row_ptr; const int32_t* col; const double* val; };
-struct CscDev { int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val; };
+// Sliced-ELL copy of a CSR matrix (slices of 32 rows; inside a window of 256 rows the
+// rows are ordered by decreasing length; slice s holds width W_s = max length entries per
+// row, column-major: entry k of slice row l at off[s] + 32 k + l; padding has value 0
+// and column 0; perm[32 s + l] = original row, -1 for padding rows).
+struct SellDev { int64_t nslices; const int64_t* off; const int32_t* perm; const int32_t* col; const double* val; };
+struct CsrDev {
+  int64_t m, n; const int64_t* row_ptr; const int32_t* col; const double* val;
+  SellDev sell;  // used when the product runs with lanes == -2
+};
+struct CscDev {
+  int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val;
+  SellDev sell;
+};
 
 // Scalar slots of the CG state kept on the device (copied to the host each iteration).
 enum {
