@@ -125,6 +125,11 @@ struct ls_handle {
   DevBuf<int64_t> row_ptr, col_ptr;
   DevBuf<int32_t> col, crow, part;
   DevBuf<double> val, cval;
+  // The device matrix is A' = P A (rows by first column): perm[new] = original row,
+  // entmap[e'] = original CSR slot of entry e' of A'.
+  DevBuf<int32_t> perm;
+  DevBuf<int64_t> entmap;
+  std::vector<int32_t> h_perm;
   lsq::SellDev sellA{}, sellB{};  // sliced-ELL copies of A and A^T (pointers below)
   DevBuf<int64_t> sellA_off, sellB_off;
   DevBuf<int32_t> sellA_perm, sellA_col, sellB_perm, sellB_col;
@@ -481,6 +486,36 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   std::vector<int32_t> hpart = to_host(part_in, (size_t)h->n);
   for (int64_t e = 0; e < nnz; ++e)
     if (!std::isfinite(hval[e])) throw LsError(LS_ERR_NONFINITE, "A has a non-finite value at entry " + std::to_string(e));
+  {
+    const std::string verr = lsq::validate_inputs(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data());
+    if (!verr.empty()) throw LsError(LS_ERR_INVALID, verr);
+  }
+  // Work with A' = P A, rows ordered by first column (min ||Ax - b|| = min ||PAx - Pb||):
+  // neighbouring rows then touch neighbouring entries of x and of A p.
+  {
+    std::vector<int32_t> perm;
+    lsq::order_rows_by_first_column(h->m, h->n, hrp.data(), hcol.data(), perm);
+    std::vector<int64_t> rp2(h->m + 1, 0), emap(nnz);
+    std::vector<int32_t> c2(nnz);
+    std::vector<double> v2(nnz);
+    for (int64_t r2 = 0; r2 < h->m; ++r2) {
+      const int32_t r = perm[r2];
+      const int64_t len = hrp[r + 1] - hrp[r];
+      rp2[r2 + 1] = rp2[r2] + len;
+      for (int64_t k = 0; k < len; ++k) {
+        c2[rp2[r2] + k] = hcol[hrp[r] + k];
+        v2[rp2[r2] + k] = hval[hrp[r] + k];
+        emap[rp2[r2] + k] = hrp[r] + k;
+      }
+    }
+    h->perm.upload(perm, st);
+    h->entmap.upload(emap, st);
+    CK(cudaStreamSynchronize(st));
+    h->h_perm.swap(perm);
+    hrp.swap(rp2);
+    hcol.swap(c2);
+    hval.swap(v2);
+  }
   lsq::HostSets hs;
   std::string err = lsq::build_host_sets(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data(), h->coarse, hs);
   if (!err.empty()) throw LsError(LS_ERR_INVALID, err);
@@ -843,7 +878,9 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
     CK(cudaSetDevice(h->dev));
     ls_status last = LS_OK;
     for (int k = 0; k < nrhs; ++k) {
-      CK(cudaMemcpyAsync(h->bv.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, h->st));
+      // b' = P b for the row-reordered device matrix
+      CK(cudaMemcpyAsync(h->q.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, h->st));
+      lsq::launch_gather(h->m, h->perm.p, h->q.p, h->bv.p, h->st);
       ls_status s = solve_core(h, 0, rtol, info);
       CK(cudaMemcpyAsync(x + (int64_t)k * h->n, h->x.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
       CK(cudaStreamSynchronize(h->st));
@@ -860,38 +897,35 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
     CK(cudaSetDevice(h->dev));
     cudaStream_t st = h->st;
     ls_status last = LS_OK;
-    DevBuf<double> xk, lam, mu;
-    xk.alloc(h->n); lam.alloc(h->n); mu.alloc(h->m);
+    DevBuf<double> xk, lam, mu, tmp, gperm, gout;
+    xk.alloc(h->n); lam.alloc(h->n); mu.alloc(h->m); tmp.alloc(h->m);
+    if (grad_vals) { gperm.alloc(h->nnz); gout.alloc(h->nnz); }
     for (int k = 0; k < nrhs; ++k) {
       CK(cudaMemcpyAsync(h->tv.p, grad_x + (int64_t)k * h->n, sizeof(double) * h->n, cudaMemcpyDefault, st));
       ls_status s = solve_core(h, 1, rtol, info);
       if (s != LS_OK) last = s;
       CK(cudaMemcpyAsync(lam.p, h->x.p, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
-      lsq::launch_spmv_csr(csr(h), lam.p, mu.p, h->lanes_csr, h->grid_csr, st);  // mu = A lambda = grad_b
-      if (grad_b)
-        CK(cudaMemcpyAsync(grad_b + (int64_t)k * h->m, mu.p, sizeof(double) * h->m, cudaMemcpyDefault, st));
+      lsq::launch_spmv_csr(csr(h), lam.p, mu.p, h->lanes_csr, h->grid_csr, st);  // mu' = A' lambda
+      if (grad_b) {  // grad_b = A lambda = P^T mu'
+        lsq::launch_scatter_idx(h->m, h->perm.p, nullptr, mu.p, tmp.p, 0, st);
+        CK(cudaMemcpyAsync(grad_b + (int64_t)k * h->m, tmp.p, sizeof(double) * h->m, cudaMemcpyDefault, st));
+      }
       if (grad_vals) {
         CK(cudaMemcpyAsync(xk.p, x + (int64_t)k * h->n, sizeof(double) * h->n, cudaMemcpyDefault, st));
-        CK(cudaMemcpyAsync(h->bv.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(tmp.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, st));
+        lsq::launch_gather(h->m, h->perm.p, tmp.p, h->bv.p, st);  // b' = P b
         lsq::launch_spmv_csr(csr(h), xk.p, h->q.p, h->lanes_csr, h->grid_csr, st);
-        lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);  // rho = b - A x
-        DevBuf<double> gv;
-        double* gdst = grad_vals;
-        cudaPointerAttributes pa{};
-        bool dev_ptr = cudaPointerGetAttributes(&pa, grad_vals) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
-        cudaGetLastError();
-        if (!dev_ptr) {
-          gv.alloc(h->nnz);
-          if (k > 0) CK(cudaMemcpyAsync(gv.p, grad_vals, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
-          gdst = gv.p;
-        }
-        lsq::launch_grad_vals(csr(h), h->q.p, lam.p, mu.p, xk.p, gdst, k > 0 ? 1 : 0, st);
-        if (!dev_ptr) CK(cudaMemcpyAsync(grad_vals, gv.p, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
-        CK(cudaStreamSynchronize(st));
+        lsq::launch_axpby(h->m, 1.0, h->bv.p, -1.0, h->q.p, h->q.p, st);  // rho' = b' - A' x
+        lsq::launch_grad_vals(csr(h), h->q.p, lam.p, mu.p, xk.p, gperm.p, k > 0 ? 1 : 0, st);
       }
       check_launch("backward");
     }
+    if (grad_vals) {  // entries of A' back to the caller's CSR order
+      lsq::launch_scatter_idx(h->nnz, nullptr, h->entmap.p, gperm.p, gout.p, 0, st);
+      CK(cudaMemcpyAsync(grad_vals, gout.p, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
+    }
     CK(cudaStreamSynchronize(st));
+    check_launch("backward");
     return last;
   });
 }
@@ -982,7 +1016,10 @@ ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap) 
     } else if (kind == LS_Q_XI) {
       const int64_t k = h->h_xi_off[i + 1] - h->h_xi_off[i];
       need(k);
-      std::memcpy(out, h->h_xi.data() + h->h_xi_off[i], sizeof(int32_t) * k);
+      // internal rows are those of A' = P A: report the caller's row numbers, ascending
+      int32_t* o = (int32_t*)out;
+      for (int64_t a = 0; a < k; ++a) o[a] = h->h_perm[h->h_xi[h->h_xi_off[i] + a]];
+      std::sort(o, o + k);
     } else if (kind == LS_Q_EIGVALS) {
       if (h->h_lam.empty()) throw LsError(LS_ERR_INVALID, "no eigensolve was run");
       const int64_t ni = h->h_om_off[i + 1] - h->h_om_off[i];

@@ -79,6 +79,38 @@ void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const dou
     }
 }
 
+void order_rows_by_first_column(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                std::vector<int32_t>& perm) {
+  // stable counting sort on the key col[row_ptr[r]] (n for an empty row)
+  std::vector<int64_t> cnt(n + 2, 0);
+  auto key = [&](int64_t r) -> int64_t { return row_ptr[r + 1] > row_ptr[r] ? col[row_ptr[r]] : n; };
+  for (int64_t r = 0; r < m; ++r) cnt[key(r) + 1]++;
+  for (int64_t k = 0; k <= n; ++k) cnt[k + 1] += cnt[k];
+  perm.assign(m, 0);
+  for (int64_t r = 0; r < m; ++r) perm[cnt[key(r)]++] = (int32_t)r;
+}
+
+std::string validate_inputs(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int N,
+                            const int32_t* part) {
+  if (m < 1 || n < 1) return "m and n must be positive";
+  if (N < 1 || N > n) return "nparts must lie in [1, n]";
+  if (n > INT32_MAX || m > INT32_MAX) return "m and n must fit in int32";
+  if (row_ptr[0] != 0) return "row_ptr[0] must be 0";
+  for (int64_t r = 0; r < m; ++r)
+    if (row_ptr[r + 1] < row_ptr[r]) return "row_ptr must be nondecreasing";
+  for (int64_t r = 0; r < m; ++r) {
+    for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+      int32_t c = col[e];
+      if (c < 0 || c >= n) return "column index out of range in row " + std::to_string(r);
+      if (e > row_ptr[r] && c <= col[e - 1])
+        return "column indices must be strictly increasing within row " + std::to_string(r);
+    }
+  }
+  for (int64_t j = 0; j < n; ++j)
+    if (part[j] < 0 || part[j] >= N) return "part[" + std::to_string(j) + "] out of range";
+  return std::string();
+}
+
 std::string build_host_sets(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
                             int N, const int32_t* part, bool with_pairs, HostSets& hs) {
   if (m < 1 || n < 1) return "m and n must be positive";

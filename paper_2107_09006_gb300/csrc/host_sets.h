@@ -73,6 +73,16 @@ struct SellHost {
 void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const double* val, int window,
                 SellHost& out);
 
+// Checks sizes, the CSR pattern (sorted, in range) and the partition ids; "" if valid.
+std::string validate_inputs(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int N,
+                            const int32_t* part);
+
+// Row order by first stored column (stable; empty rows last): perm[new] = old row.
+// Rows of a least-squares problem may be permuted freely; this order keeps the
+// vector entries that neighbouring rows and columns touch close in memory.
+void order_rows_by_first_column(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                std::vector<int32_t>& perm);
+
 // Validates the CSR pattern and the partition and fills hs.  Returns an empty
 // string on success, else the reason the input is invalid.  col must be strictly
 // increasing within each row; part[j] must lie in [0, N).

@@ -233,6 +233,20 @@ __global__ void k_axpby(int64_t n, double alpha, const double* __restrict__ a, d
     out[k] = alpha * a[k] + (b ? beta * b[k] : 0.0);
 }
 
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ idx, const double* __restrict__ src,
+                         double* __restrict__ dst) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[idx[k]];
+}
+
+__global__ void k_scatter_idx(int64_t n, const int32_t* __restrict__ i32, const int64_t* __restrict__ i64,
+                              const double* __restrict__ src, double* __restrict__ dst, int accumulate) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i32 ? (int64_t)i32[k] : i64[k];
+    dst[t] = accumulate ? dst[t] + src[k] : src[k];
+  }
+}
+
 __global__ void k_fill(int64_t n, double v, double* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = v;
@@ -375,6 +389,15 @@ void launch_axpby(int64_t n, double alpha, const double* a, double beta, const d
 
 void launch_fill(int64_t n, double v, double* out, cudaStream_t st) {
   k_fill<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, v, out);
+}
+
+void launch_gather(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t st) {
+  k_gather<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx, src, dst);
+}
+
+void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,
+                        int accumulate, cudaStream_t st) {
+  k_scatter_idx<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx32, idx64, src, dst, accumulate);
 }
 
 void launch_scatter(const ScatterArgs& a, cudaStream_t st) {

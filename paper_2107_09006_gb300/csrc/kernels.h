@@ -49,6 +49,11 @@ void launch_dot(int64_t n, const double* a, const double* b, const DotSite& ds, 
 void launch_axpby(int64_t n, double alpha, const double* a, double beta, const double* b, double* out,
                   cudaStream_t st);
 void launch_fill(int64_t n, double v, double* out, cudaStream_t st);
+// dst[i] = src[idx[i]] for i < n
+void launch_gather(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t st);
+// dst[idx[i]] = src[i] (int32 or int64 indices; accumulate: dst[idx[i]] += src[i])
+void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,
+                        int accumulate, cudaStream_t st);
 
 struct ScatterArgs {
   int64_t n;
