@@ -75,6 +75,12 @@ typedef struct {
     int use_graph;     /* 1: replay each CG iteration as a captured CUDA graph          */
     int time_kernels;  /* 1: time the local-solve and sparse-product launches of each
                           iteration with CUDA events (reported in ls_info)           */
+    int equilibrate;   /* 1: build the preconditioner for the column-equilibrated problem
+                          A S (S = diag(1/||A(:,j)||)) and apply S M_S^{-1} S.  Without
+                          shifts the method is invariant under column scaling; with the
+                          shifts delta and s of Section 4.1.2 it is not, and badly scaled
+                          columns then see a shift far above their diagonal.  0 (the
+                          default) follows the paper as written.                      */
 } ls_options;
 
 typedef struct {
@@ -149,6 +155,12 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
  * grad_b or grad_vals may be NULL to skip them. */
 ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x,
                       int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info);
+
+/* Replace the values of A (same pattern; val[nnz] in the caller's CSR order, host or
+ * device) in the operator the solves apply; the preconditioner built by ls_setup is
+ * kept as it is (it stays a valid SPD preconditioner; rebuild with ls_setup when the
+ * values move far).  Used by finite-difference checks and optimization loops. */
+ls_status ls_update_values(ls_handle* h, const double* val);
 
 /* Release everything the handle owns.  NULL is ignored. */
 void ls_free(ls_handle* h);

@@ -26,7 +26,8 @@ class ls_options(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("nev_max", ctypes.c_int), ("delta_rel", ctypes.c_double),
                 ("s_rel", ctypes.c_double), ("factor_prec", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
-                ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int)]
+                ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
+                ("equilibrate", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -67,6 +68,7 @@ def _load():
         "ls_apply_normal": (ctypes.c_int, [vp, vp, vp]),
         "ls_query": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, i64]),
         "ls_build_index_sets": (ctypes.c_int, [i64, i64, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ls_update_values": (ctypes.c_int, [vp, vp]),
         "ls_normal_product_noalloc": (ctypes.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]),
         "ls_noalloc_last_error": (ctypes.c_char_p, []),
     }
@@ -81,7 +83,7 @@ _lib = _load()
 LIBRARY_PATH = _LIB_PATH
 EXPORTED = ("ls_default_options", "ls_setup", "ls_solve", "ls_backward", "ls_free", "ls_last_error",
             "ls_handle_info", "ls_apply_preconditioner", "ls_apply_normal", "ls_query", "ls_build_index_sets",
-            "ls_normal_product_noalloc", "ls_noalloc_last_error")
+            "ls_normal_product_noalloc", "ls_noalloc_last_error", "ls_update_values")
 
 
 def _ptr(a) -> int | None:
@@ -140,6 +142,12 @@ def ls_backward(h, b, x, grad_x, nrhs, rtol, grad_b=None, grad_vals=None) -> dic
     _check(_lib.ls_backward(h, _ptr(b), _ptr(x), _ptr(grad_x), int(nrhs), float(rtol), _ptr(grad_b),
                             _ptr(grad_vals), ctypes.byref(info)))
     return info.as_dict()
+
+
+def ls_update_values(h, val):
+    """New values of A (same pattern, caller's CSR order) for the operator; the
+    preconditioner is kept."""
+    _check(_lib.ls_update_values(h, _ptr(val)))
 
 
 def ls_free(h):

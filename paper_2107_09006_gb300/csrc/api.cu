@@ -73,6 +73,21 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// data[e] *= scale[idx[e]]
+__global__ void k_scale_by_gather(int64_t n, const int32_t* idx, const double* scale, double* data) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    data[e] *= scale[idx[e]];
+}
+
+// Zbar_i[t, jj] *= scale[interior column jj of subdomain i]  (one block per subdomain)
+__global__ void k_scale_zbar(const int32_t* coff, const int64_t* zoff, const int64_t* int_off,
+                             const int32_t* int_glob, const double* scale, double* Z) {
+  const int i = blockIdx.x;
+  const int k = coff[i + 1] - coff[i];
+  const int64_t io = int_off[i], nI = int_off[i + 1] - io;
+  for (int64_t e = threadIdx.x; e < (int64_t)k * nI; e += blockDim.x) Z[zoff[i] + e] *= scale[int_glob[io + e % nI]];
+}
+
 __global__ void k_set_diag(double* A, int64_t ld, int64_t from, int64_t to, double v) {
   for (int64_t k = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < to; k += (int64_t)gridDim.x * blockDim.x)
     A[k * ld + k] = v;
@@ -134,6 +149,7 @@ struct ls_handle {
   DevBuf<int64_t> sellA_off, sellB_off;
   DevBuf<int32_t> sellA_perm, sellA_col, sellB_perm, sellB_col;
   DevBuf<double> sellA_val, sellB_val;
+  DevBuf<int64_t> cperm, sellA_src, sellB_src;  // source A' CSR slot of the CSC / ELL copies
 
   DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
   DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
@@ -436,6 +452,14 @@ std::vector<T> to_host(const T* src, size_t count) {
   return v;
 }
 
+// The CSC and sliced-ELL copies of A' take their values from the CSR values h->val.
+void refresh_value_copies(ls_handle* h) {
+  cudaStream_t st = h->st;
+  lsq::launch_gather64(h->nnz, h->cperm.p, h->val.p, h->cval.p, st);
+  lsq::launch_gather64((int64_t)h->sellA_src.n, h->sellA_src.p, h->val.p, h->sellA_val.p, st);
+  lsq::launch_gather64((int64_t)h->sellB_src.n, h->sellB_src.p, h->val.p, h->sellB_val.p, st);
+}
+
 // Lanes per row (A) and per column (A^T) of the two sparse products, picked by timing
 // every power of two on the actual matrix (three launches each, CUDA events).
 void autotune_spmv(ls_handle* h) {
@@ -516,6 +540,15 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     hcol.swap(c2);
     hval.swap(v2);
   }
+  // Optional column equilibration: the preconditioner is built for A S.
+  std::vector<double> hval_orig, colscale;
+  if (h->opt.equilibrate) {
+    colscale.assign(h->n, 0.0);
+    for (int64_t e = 0; e < nnz; ++e) colscale[hcol[e]] += hval[e] * hval[e];
+    for (auto& s : colscale) s = s > 0.0 ? 1.0 / std::sqrt(s) : 1.0;
+    hval_orig = hval;
+    for (int64_t e = 0; e < nnz; ++e) hval[e] *= colscale[hcol[e]];
+  }
   lsq::HostSets hs;
   std::string err = lsq::build_host_sets(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data(), h->coarse, hs);
   if (!err.empty()) throw LsError(LS_ERR_INVALID, err);
@@ -541,6 +574,12 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     lsq::SellHost sa, sb;
     lsq::build_sell(h->m, hrp.data(), hcol.data(), hval.data(), 256, sa);
     lsq::build_sell(h->n, hs.csc_ptr.data(), hs.csc_row.data(), cv.data(), 256, sb);
+    // where every stored copy of an entry comes from (A' CSR slot), for ls_update_values
+    for (auto& e : sb.src)
+      if (e >= 0) e = hs.csc_perm[e];
+    h->cperm.upload(hs.csc_perm, st);
+    h->sellA_src.upload(sa.src, st);
+    h->sellB_src.upload(sb.src, st);
     h->sellA.nslices = sa.nslices;
     h->sellA_off.upload(sa.off, st); h->sellA_perm.upload(sa.perm, st);
     h->sellA_col.upload(sa.col, st); h->sellA_val.upload(sa.val, st);
@@ -789,6 +828,19 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   }
   Bst.release(); Ctst.release(); Bidiag.release();
 
+  if (h->opt.equilibrate) {
+    // the operator is A itself; M^{-1} = S M_S^{-1} S with S folded into the local
+    // gather/scatter scales and into the rows of the coarse basis
+    CK(cudaMemcpyAsync(h->val.p, hval_orig.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+    refresh_value_copies(h);
+    DevBuf<double> sdev;
+    sdev.upload(colscale, st);
+    k_scale_by_gather<<<1024, 256, 0, st>>>(h->total_local, h->om_glob.p, sdev.p, h->eqs.p);
+    if (h->n0 > 0) k_scale_zbar<<<N, 256, 0, st>>>(h->coff.p, h->zoff.p, h->int_off.p, h->int_glob.p, sdev.p, h->Z.p);
+    CK(cudaStreamSynchronize(st));
+    check_launch("column equilibration");
+  }
+
   // work vectors
   const int64_t mm = std::max(h->m, h->n);
   h->x.alloc(h->n); h->r.alloc(h->n); h->r_old.alloc(h->n); h->z.alloc(h->n); h->p.alloc(h->n);
@@ -829,6 +881,7 @@ void ls_default_options(ls_options* o) {
   o->eig_tol = 1e-11;
   o->use_graph = 1;
   o->time_kernels = 0;
+  o->equilibrate = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -927,6 +980,23 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
     CK(cudaStreamSynchronize(st));
     check_launch("backward");
     return last;
+  });
+}
+
+ls_status ls_update_values(ls_handle* h, const double* val) {
+  return guarded([&]() -> ls_status {
+    if (!h || !val) throw LsError(LS_ERR_INVALID, "null argument");
+    CK(cudaSetDevice(h->dev));
+    cudaStream_t st = h->st;
+    const int64_t nnz = h->nnz;
+    DevBuf<double> tmp;
+    tmp.alloc(nnz);
+    CK(cudaMemcpyAsync(tmp.p, val, sizeof(double) * nnz, cudaMemcpyDefault, st));
+    lsq::launch_gather64(nnz, h->entmap.p, tmp.p, h->val.p, st);  // A' = P A, CSR
+    refresh_value_copies(h);
+    CK(cudaStreamSynchronize(st));
+    check_launch("value update");
+    return LS_OK;
   });
 }
 

@@ -68,6 +68,7 @@ void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const dou
   }
   out.col.assign(out.off[ns], 0);
   out.val.assign(out.off[ns], 0.0);
+  out.src.assign(out.off[ns], -1);
   for (int64_t s = 0; s < ns; ++s)
     for (int l = 0; l < 32; ++l) {
       const int32_t r = out.perm[s * 32 + l];
@@ -75,6 +76,7 @@ void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const dou
       for (int64_t e = ptr[r], k = 0; e < ptr[r + 1]; ++e, ++k) {
         out.col[out.off[s] + 32 * k + l] = idx[e];
         out.val[out.off[s] + 32 * k + l] = val[e];
+        out.src[out.off[s] + 32 * k + l] = e;
       }
     }
 }

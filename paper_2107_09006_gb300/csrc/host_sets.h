@@ -69,6 +69,7 @@ struct SellHost {
   std::vector<int64_t> off;
   std::vector<int32_t> perm, col;
   std::vector<double> val;
+  std::vector<int64_t> src;  // source CSR slot of every stored entry (-1: padding)
 };
 void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const double* val, int window,
                 SellHost& out);

@@ -239,6 +239,14 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ idx, const doubl
     dst[k] = src[idx[k]];
 }
 
+__global__ void k_gather64(int64_t n, const int64_t* __restrict__ idx, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx[k];
+    dst[k] = t >= 0 ? src[t] : 0.0;
+  }
+}
+
 __global__ void k_scatter_idx(int64_t n, const int32_t* __restrict__ i32, const int64_t* __restrict__ i64,
                               const double* __restrict__ src, double* __restrict__ dst, int accumulate) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -393,6 +401,11 @@ void launch_fill(int64_t n, double v, double* out, cudaStream_t st) {
 
 void launch_gather(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t st) {
   k_gather<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx, src, dst);
+}
+
+void launch_gather64(int64_t n, const int64_t* idx, const double* src, double* dst, cudaStream_t st) {
+  if (n <= 0) return;
+  k_gather64<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx, src, dst);
 }
 
 void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,

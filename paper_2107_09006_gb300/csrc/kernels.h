@@ -51,6 +51,8 @@ void launch_axpby(int64_t n, double alpha, const double* a, double beta, const d
 void launch_fill(int64_t n, double v, double* out, cudaStream_t st);
 // dst[i] = src[idx[i]] for i < n
 void launch_gather(int64_t n, const int32_t* idx, const double* src, double* dst, cudaStream_t st);
+// dst[i] = src[idx[i]], or 0 where idx[i] < 0 (int64 indices)
+void launch_gather64(int64_t n, const int64_t* idx, const double* src, double* dst, cudaStream_t st);
 // dst[idx[i]] = src[i] (int32 or int64 indices; accumulate: dst[idx[i]] += src[i])
 void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,
                         int accumulate, cudaStream_t st);

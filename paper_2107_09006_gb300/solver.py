@@ -6,7 +6,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (ls_setup, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info,
+from . import (ls_setup, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info, ls_update_values,
                ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI,
                LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE)
 
@@ -80,6 +80,12 @@ class Solver:
         info = ls_backward(self.h, b, x, g, nrhs, rtol, gb, gv)
         return gb, gv, info
 
+    def update_values(self, val):
+        """Replace A's values in the operator (the preconditioner is kept)."""
+        v = _dev(val, torch.float64, self.device)
+        self._fence()
+        ls_update_values(self.h, v)
+
     def apply_preconditioner(self, r, which=0):
         r = _dev(r, torch.float64, self.device)
         z = torch.empty_like(r)
@@ -128,14 +134,15 @@ class Solver:
 
 class LSSolve(torch.autograd.Function):
     """x = LSSolve.apply(vals, b, solver, rtol): the LS solution for A with the solver's
-    pattern and values ``vals``.  Backward is the adjoint solve lambda = C^{-1} grad_x
-    with the same preconditioner: grad_b = A lambda, grad_vals = rho lambda^T - (A lambda) x^T
-    on the stored entries (rho = b - A x).  The preconditioner is built from the
-    solver's own values; ``vals`` must equal them (the solver is rebuilt by the caller
-    when A changes)."""
+    pattern and the values ``vals`` (caller's CSR order).  Backward is the adjoint solve
+    lambda = C^{-1} grad_x with the same preconditioner: grad_b = A lambda,
+    grad_vals = rho lambda^T - (A lambda) x^T on the stored entries (rho = b - A x).
+    The operator takes ``vals`` (ls_update_values); the preconditioner stays the one
+    the solver was set up with."""
 
     @staticmethod
     def forward(ctx, vals, b, solver, rtol=1e-10):
+        solver.update_values(vals.detach())
         x, info = solver.solve(b.detach(), rtol)
         ctx.solver, ctx.rtol = solver, rtol
         ctx.save_for_backward(b.detach(), x)
