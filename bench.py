@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-side", type=int, default=256, help="grid side of the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision"],
+                    help="solve: the timed benchmark line; nsweep: iterations/setup vs subdomain count "
+                         "(blocks 128/64/32); precision: errors of every form on the column-scaled workload")
     return ap.parse_args()
 
 
@@ -317,9 +320,126 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _device_setup():
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch, dev
+
+
+def run_nsweep(args):
+    """Subdomain-count sweep on the n = 1M grid: for blocks of 128, 64 and 32 columns a
+    side (N = 64, 256, 1024) the setup split (index sets + factors, eigensolve + coarse),
+    n0, iterations to rtol and the solve time; one JSON line per N and a summary."""
+    torch, dev = _device_setup()
+    from paper_2107_09006_gb300 import Solver, ls_solve
+    from workloads import config_scale
+    rows = []
+    for block in (128, 64, 32):
+        P = config_scale(side=args.side, block=block)
+        b = torch.as_tensor(P.b, device=dev)
+        x = torch.empty(P.n, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        t = time.time()
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   nev_max=args.nev, factor_prec=args.prec, time_kernels=1, maxit=5000)
+        torch.cuda.synchronize(dev)
+        setup = time.time() - t
+        si = S.info()
+        for _ in range(max(args.warmup, 1)):
+            ls_solve(S.h, b, 1, args.rtol, x)
+        ts, infos = [], []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(ls_solve(S.h, b, 1, args.rtol, x))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1) / 1000.0)
+        it = infos[-1]
+        row = {"N": P.nparts, "block": block, "n0": si["n0"], "kmin": si["kmin"], "kmax": si["kmax"],
+               "tau_used": si["tau_used"], "setup_s": setup, "eig_coarse_s": si["t_eig"],
+               "iterations": it["iters"], "relres_true": it["relres_true"], "kappa_lanczos": it["kappa_lanczos"],
+               "solve_s": statistics.median(ts), "ms_local": it["ms_local"] / max(it["local_launches"], 1),
+               "ms_coarse_per_iter": it["ms_coarse"] / max(it["iters"], 1),
+               "ms_spmv_per_iter": it["ms_spmv"] / max(it["iters"], 1), "fac_elems": S.storage()["fac_elems"]}
+        log(f"[nsweep] {json.dumps(row)}")
+        rows.append(row)
+        S.close()
+        del S
+        torch.cuda.empty_cache()
+    its = [r["iterations"] for r in rows]
+    print(json.dumps({"report": "nsweep", "workload": f"grid{args.side}-r3k8, nev_max {args.nev}, tau auto, "
+                      f"form {args.prec}, rtol {args.rtol:g}", "rows": rows,
+                      "iterations_max_over_min": max(its) / min(its)}), flush=True)
+
+
+def run_precision(args):
+    """Column-scaled n = 1M workload (columns scaled by 10**U(-3, 3)): the FP64 form run
+    to rtol 1e-13 with column equilibration is the reference solution; every factor
+    precision, with the paper's construction as written and with equilibration, is
+    solved to 1e-8 and 1e-10 and its relative error against the reference reported."""
+    torch, dev = _device_setup()
+    import numpy as np
+    from paper_2107_09006_gb300 import Solver, ls_solve
+    from workloads import config_precision
+    P = config_precision(side=args.side, block=args.block)
+    b = torch.as_tensor(P.b, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(prec, eq, maxit):
+        t = time.time()
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   nev_max=args.nev, factor_prec=prec, maxit=maxit, equilibrate=eq)
+        torch.cuda.synchronize(dev)
+        return S, time.time() - t
+
+    def solve(S, rtol):
+        x = torch.empty(P.n, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ls_solve(S.h, b, 1, rtol, x, raise_on_fail=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return x, info, e0.elapsed_time(e1) / 1000.0
+
+    S, _ = make("f64", 1, 2000)
+    xref, iref, _ = solve(S, 1e-13)
+    S.close()
+    nref = float(torch.linalg.norm(xref))
+    rows = []
+    for eq in (1, 0):
+        for prec in ("f64", "f32", "bf16"):
+            S, setup = make(prec, eq, 500 if eq else 4000)
+            n0 = S.info()["n0"]
+            for rtol in (1e-8, 1e-10):
+                x, info, sec = solve(S, rtol)
+                err = float(torch.linalg.norm(x - xref)) / nref
+                row = {"form": prec, "construction": "equilibrated" if eq else "paper", "rtol": rtol,
+                       "iterations": info["iters"], "restarts": info["restarts"], "status": info["status"],
+                       "relres_true": info["relres_true"], "rel_error_vs_fp64_1e-13": err, "solve_s": sec,
+                       "setup_s": setup, "n0": n0}
+                log(f"[precision] {json.dumps(row)}")
+                rows.append(row)
+            S.close()
+            del S
+            torch.cuda.empty_cache()
+    print(json.dumps({"report": "precision", "workload": f"grid{args.side}-r3k8-N{P.nparts} columns scaled by "
+                      f"10**U(-3,3), nev_max {args.nev}, tau auto",
+                      "reference": {"form": "f64", "construction": "equilibrated", "rtol": 1e-13,
+                                    "iterations": iref["iters"], "relres_true": iref["relres_true"]},
+                      "rows": rows}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "nsweep":
+        run_nsweep(a)
+    elif a.mode == "precision":
+        run_precision(a)
     else:
         run_ours(a)

@@ -596,6 +596,17 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->total_blocks = hs.blk_off[N];
   h->fac_elems = hs.fac_elems;
   h->max_nb = hs.max_nb;
+  {
+    // the local solve keeps one subdomain's right-hand side in shared memory
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+    const size_t need = lsq::local_solve_smem(h->opt.factor_prec, h->max_nb);
+    if (need > (size_t)optin)
+      throw LsError(LS_ERR_UNSUPPORTED, "largest subdomain (" + std::to_string((int64_t)h->max_nb * 32) +
+                                            " padded columns) needs " + std::to_string(need) +
+                                            " B of shared memory in the local solve; the device allows " +
+                                            std::to_string(optin) + " B: use more subdomains");
+  }
   h->om_off.upload(hs.om_off, st);
   h->om_glob.upload(hs.om_glob, st);
   h->om_int.upload(hs.om_int, st);
