@@ -135,14 +135,37 @@ ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* 
                    const double* val, int32_t nparts, const int32_t* part, int overlap,
                    const ls_options* opt, void* stream, ls_handle** out);
 
+/* Batched setup: nprob independent least-squares problems in one handle, given as one
+ * block-diagonal matrix (the "many problems share a launch" pattern).
+ *   m_off[nprob+1], n_off[nprob+1]  host int64 offsets: problem q owns the rows
+ *                   [m_off[q], m_off[q+1]) and the columns [n_off[q], n_off[q+1]);
+ *                   a row may only touch the columns of its own problem
+ *   row_ptr, col, val  the whole matrix in CSR (m = m_off[nprob], n = n_off[nprob])
+ *   part[n]         subdomain ids; the ids of problem q form one range, in problem
+ *                   order (problem 0 owns ids 0 .. N_1-1, problem 1 the next ones, ...)
+ * Every problem is set up as if alone: its own delta = delta_rel ||C_q||_F, its own
+ * automatic threshold (tau <= 0) and its own dense coarse block.  Other arguments and
+ * errors as ls_setup (LS_ERR_INVALID also for a row or subdomain crossing problems). */
+ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
+                           const int64_t* row_ptr, const int32_t* col, const double* val,
+                           int32_t nparts, const int32_t* part, int overlap, const ls_options* opt,
+                           void* stream, ls_handle** out);
+
 /* Solve min ||A x - b|| for nrhs right-hand sides by PCG on C x = A^T b with x_0 = 0.
  *   b[m * nrhs]     column-major right-hand sides (host or device)
  *   rtol            stop when ||A^T (b - A x)|| <= rtol ||A^T b|| (true residual,
  *                   recomputed whenever the recursive residual passes the test; if
  *                   the true one fails, CG restarts from it)
  *   x[n * nrhs]     output, column-major (host or device)
- *   info            statistics of the last right-hand side (may be NULL)
- * Errors: LS_ERR_NOT_CONVERGED (x holds the last iterate), LS_ERR_NONFINITE. */
+ *   info            statistics (may be NULL)
+ * One right-hand side on a single-problem handle runs the single-vector path.
+ * Otherwise (nrhs in 1..32, or a batched handle) all right-hand sides and problems
+ * advance together: every kernel of an iteration serves all of them, each (problem,
+ * right-hand side) pair keeps its own CG scalars and stops on its own test (its
+ * ||A_q^T b_q|| in the denominator), and info carries the largest iteration count and
+ * true residual; the per-pair values are in ls_query(LS_Q_BATCH).
+ * Errors: LS_ERR_NOT_CONVERGED (x holds the last iterate), LS_ERR_NONFINITE,
+ * LS_ERR_UNSUPPORTED (nrhs > 32 on the multi right-hand-side path). */
 ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x,
                    ls_info* info);
 
@@ -152,7 +175,7 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
  *   grad_vals[k] = rho_r lambda_c - (A lambda)_r x_c    for CSR entry k = (r, c),
  *                  rho = b - A x                        (summed over right-hand sides)
  * b, x, grad_x are the forward inputs/outputs (column-major, host or device);
- * grad_b or grad_vals may be NULL to skip them. */
+ * grad_b or grad_vals may be NULL to skip them.  Batched handles: LS_ERR_UNSUPPORTED. */
 ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x,
                       int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info);
 
@@ -174,7 +197,8 @@ ls_status ls_handle_info(const ls_handle* h, ls_info* info);
 /* ---- inspection calls used by tests and benchmarks ------------------------------ */
 
 /* z = M^{-1} r for one vector (host or device pointers, n entries each); which = 0:
- * the full two-level operator, 1: the local sum only, 2: the coarse term only. */
+ * the full two-level operator, 1: the local sum only, 2: the coarse term only.
+ * Batched handles: LS_ERR_UNSUPPORTED. */
 ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int which);
 
 /* w = A^T (A p) for one vector (host or device pointers, n entries each). */
@@ -189,9 +213,12 @@ typedef enum {
     LS_Q_ZBAR = 4,     /* float64[k_i * n_I,i]: coarse basis of subdomain i, one
                           vector after another, over Omega_I,i ascending            */
     LS_Q_EIGSTEPS = 5, /* int32[N]: Lanczos steps per subdomain                     */
-    LS_Q_STORAGE = 6   /* int64[8]: factor elements (all subdomains), sum n_i, block
+    LS_Q_STORAGE = 6,  /* int64[8]: factor elements (all subdomains), sum n_i, block
                           rows, coarse-basis elements, n0, padded n0, nnz(A), factor
                           precision (ls_precision)                                  */
+    LS_Q_BATCH = 7     /* float64[2 * nprob * nrhs] of the last multi right-hand-side
+                          solve: iterations, then true relative residuals, each
+                          indexed [problem * nrhs + rhs]                              */
 } ls_query_kind;
 
 /* Copy one inspected array to the host buffer out (capacity cap elements of the

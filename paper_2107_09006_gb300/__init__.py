@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libls_schwarz.so")
 LS_OK, LS_ERR_INVALID, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_FACTOR, LS_ERR_EIGEN, LS_ERR_NOT_CONVERGED, \
     LS_ERR_NONFINITE, LS_ERR_DEVICE_TIMEOUT, LS_ERR_UNSUPPORTED = range(10)
 LS_PREC_F64, LS_PREC_F32, LS_PREC_BF16 = 0, 1, 2
-LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE = range(7)
+LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH = range(8)
 _PREC = {"f64": LS_PREC_F64, "f32": LS_PREC_F32, "bf16": LS_PREC_BF16}
 
 
@@ -59,6 +59,8 @@ def _load():
         "ls_default_options": (None, [ctypes.POINTER(ls_options)]),
         "ls_setup": (ctypes.c_int, [i64, i64, vp, vp, vp, i32, vp, ctypes.c_int, ctypes.POINTER(ls_options), vp,
                                     ctypes.POINTER(vp)]),
+        "ls_setup_batched": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, i32, vp, ctypes.c_int,
+                                            ctypes.POINTER(ls_options), vp, ctypes.POINTER(vp)]),
         "ls_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, dbl, vp, ctypes.POINTER(ls_info)]),
         "ls_backward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, dbl, vp, vp, ctypes.POINTER(ls_info)]),
         "ls_free": (None, [vp]),
@@ -81,7 +83,7 @@ def _load():
 
 _lib = _load()
 LIBRARY_PATH = _LIB_PATH
-EXPORTED = ("ls_default_options", "ls_setup", "ls_solve", "ls_backward", "ls_free", "ls_last_error",
+EXPORTED = ("ls_default_options", "ls_setup", "ls_setup_batched", "ls_solve", "ls_backward", "ls_free", "ls_last_error",
             "ls_handle_info", "ls_apply_preconditioner", "ls_apply_normal", "ls_query", "ls_build_index_sets",
             "ls_normal_product_noalloc", "ls_noalloc_last_error", "ls_update_values")
 
@@ -124,6 +126,18 @@ def ls_setup(m, n, row_ptr, col, val, nparts, part, overlap=1, opt=None, stream=
     o = opt if opt is not None else ls_default_options()
     _check(_lib.ls_setup(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), int(nparts), _ptr(part),
                          int(overlap), ctypes.byref(o), stream, ctypes.byref(h)))
+    return h.value
+
+
+def ls_setup_batched(m_off, n_off, row_ptr, col, val, nparts, part, overlap=1, opt=None, stream=None):
+    """Batched setup of independent problems given as one block-diagonal CSR matrix;
+    m_off, n_off: host int64 offsets of the problems' rows and columns."""
+    mo = np.ascontiguousarray(m_off, dtype=np.int64)
+    no = np.ascontiguousarray(n_off, dtype=np.int64)
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else ls_default_options()
+    _check(_lib.ls_setup_batched(int(len(mo) - 1), _ptr(mo), _ptr(no), _ptr(row_ptr), _ptr(col), _ptr(val),
+                                 int(nparts), _ptr(part), int(overlap), ctypes.byref(o), stream, ctypes.byref(h)))
     return h.value
 
 

@@ -20,58 +20,7 @@ namespace {
 
 thread_local std::string g_err;
 
-struct LsError : std::runtime_error {
-  ls_status st;
-  LsError(ls_status s, const std::string& m) : std::runtime_error(m), st(s) {}
-};
 
-#define CK(call)                                                                              \
-  do {                                                                                        \
-    cudaError_t e_ = (call);                                                                  \
-    if (e_ != cudaSuccess)                                                                    \
-      throw LsError(e_ == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA,               \
-                    std::string(#call) + ": " + cudaGetErrorString(e_));                      \
-  } while (0)
-
-template <class T>
-struct DevBuf {
-  T* p = nullptr;
-  size_t n = 0;
-  DevBuf() = default;
-  DevBuf(const DevBuf&) = delete;
-  DevBuf& operator=(const DevBuf&) = delete;
-  ~DevBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-  }
-  void alloc(size_t count) {
-    release();
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      throw LsError(LS_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
-    }
-    n = count;
-  }
-  void zero(cudaStream_t st) { CK(cudaMemsetAsync(p, 0, n * sizeof(T), st)); }
-  void upload(const std::vector<T>& v, cudaStream_t st) {
-    alloc(v.size());
-    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  }
-  template <class U>
-  void upload_from(const U* src, size_t count, cudaStream_t st) {
-    alloc(count);
-    if (count) CK(cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyDefault, st));
-  }
-};
-
-double now_s() {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
 
 // data[e] *= scale[idx[e]]
 __global__ void k_scale_by_gather(int64_t n, const int32_t* idx, const double* scale, double* data) {
@@ -129,89 +78,17 @@ double tridiag_extreme(const std::vector<double>& d, const std::vector<double>& 
 
 }  // namespace
 
-struct ls_handle {
-  int dev = 0;
-  cudaStream_t st = nullptr;
-  bool own_stream = false;
-  ls_options opt{};
-  int64_t m = 0, n = 0, nnz = 0;
-  int N = 0, lanes_csr = 8, lanes_csc = 32, grid_csr = 0, grid_csc = 0, prec = 0;
 
-  DevBuf<int64_t> row_ptr, col_ptr;
-  DevBuf<int32_t> col, crow, part;
-  DevBuf<double> val, cval;
-  // The device matrix is A' = P A (rows by first column): perm[new] = original row,
-  // entmap[e'] = original CSR slot of entry e' of A'.
-  DevBuf<int32_t> perm;
-  DevBuf<int64_t> entmap;
-  std::vector<int32_t> h_perm;
-  lsq::SellDev sellA{}, sellB{};  // sliced-ELL copies of A and A^T (pointers below)
-  DevBuf<int64_t> sellA_off, sellB_off;
-  DevBuf<int32_t> sellA_perm, sellA_col, sellB_perm, sellB_col;
-  DevBuf<double> sellA_val, sellB_val;
-  DevBuf<int64_t> cperm, sellA_src, sellB_src;  // source A' CSR slot of the CSC / ELL copies
+#include "handle.h"
 
-  DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
-  DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
-  DevBuf<uint8_t> om_int;
-  DevBuf<double> eqs, L64;
-  DevBuf<float> L32, tsc;
-  DevBuf<__nv_bfloat16> L16;
-  int max_nb = 0;
-  int64_t total_local = 0, total_blocks = 0, fac_elems = 0;
-
-  bool coarse = false;
-  int64_t n0 = 0, n0p = 0;
-  DevBuf<int32_t> coff;
-  DevBuf<int64_t> zoff;
-  DevBuf<double> Z, Xinv;
-
-  DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
-  DevBuf<double> parts, scal, ahist, bhist;
-  DevBuf<unsigned> counters;  // ticket counters of the fused reductions
-  DevBuf<int> ctr;
-  double* pin = nullptr;  // pinned copy of the scalar slots
-  int hist_cap = 0;
-
-  cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // kernel timing
-
-  // host copies for queries
-  std::vector<int64_t> h_om_off, h_xi_off;
-  std::vector<int32_t> h_om_paper, h_xi, h_nI, h_k, h_steps;
-  std::vector<double> h_lam;
-  int kwant_cap = 0;
-  ls_info sinfo{};
-
-  ~ls_handle() {
-    if (dev >= 0) cudaSetDevice(dev);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-    if (pin) cudaFreeHost(pin);
-    if (own_stream && st) cudaStreamDestroy(st);
-  }
-};
+using namespace lsi;
 
 namespace {
-
-lsq::CsrDev csr(const ls_handle* h) {
-  return lsq::CsrDev{h->m, h->n, h->row_ptr.p, h->col.p, h->val.p,
-                     lsq::SellDev{h->sellA.nslices, h->sellA_off.p, h->sellA_perm.p, h->sellA_col.p, h->sellA_val.p}};
-}
-lsq::CscDev csc(const ls_handle* h) {
-  return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p,
-                     lsq::SellDev{h->sellB.nslices, h->sellB_off.p, h->sellB_perm.p, h->sellB_col.p, h->sellB_val.p}};
-}
 
 lsq::DotSite site(ls_handle* h, int slot, int counter, int out2 = 0) {
   return lsq::DotSite{h->parts.p, lsq::kMaxGrid, h->counters.p + counter, h->scal.p + slot, out2};
 }
 
-void check_launch(const char* what) {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) throw LsError(LS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
 
 // z = M^{-1} r (which: 0 both terms, 1 local only, 2 coarse only) with the fused dots
 // r.z (and r_old.z for the flexible recurrence) into the partial arrays.
@@ -514,6 +391,11 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     const std::string verr = lsq::validate_inputs(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data());
     if (!verr.empty()) throw LsError(LS_ERR_INVALID, verr);
   }
+  {
+    const std::string berr = lsq::validate_batch(h->m, h->n, hrp.data(), hcol.data(), h->N, hpart.data(), h->nprob,
+                                                 h->h_m_off.data(), h->h_n_off.data(), h->h_N_off, h->prob_of_sub);
+    if (!berr.empty()) throw LsError(LS_ERR_INVALID, berr);
+  }
   // Work with A' = P A, rows ordered by first column (min ||Ax - b|| = min ||PAx - Pb||):
   // neighbouring rows then touch neighbouring entries of x and of A p.
   {
@@ -596,6 +478,10 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->total_blocks = hs.blk_off[N];
   h->fac_elems = hs.fac_elems;
   h->max_nb = hs.max_nb;
+  h->wmax = 0;
+  for (int i = 0; i < h->N; ++i)
+    for (int64_t b = hs.blk_off[i]; b < hs.blk_off[i + 1]; ++b)
+      h->wmax = std::max<int>(h->wmax, (int)(b - hs.blk_off[i]) - hs.blk_tf[b] + 1);
   {
     // the local solve keeps one subdomain's right-hand side in shared memory
     int optin = 0;
@@ -659,15 +545,23 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   CK(cudaMemcpyAsync(hctn2.data(), ctn2.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   check_launch("norms");
-  double cf2 = 0.0;
-  for (int i = 0; i < N; ++i) cf2 += hcn2[i];
-  const double delta = h->opt.delta_rel * std::sqrt(cf2);
+  // delta_q = delta_rel ||C_q||_F for each independent problem q (Section 4.1.2)
+  std::vector<double> hdsub(N);
+  h->h_delta.assign(h->nprob, 0.0);
+  for (int q = 0; q < h->nprob; ++q) {
+    double cf2 = 0.0;
+    for (int i = h->h_N_off[q]; i < h->h_N_off[q + 1]; ++i) cf2 += hcn2[i];
+    h->h_delta[q] = h->opt.delta_rel * std::sqrt(cf2);
+    for (int i = h->h_N_off[q]; i < h->h_N_off[q + 1]; ++i) hdsub[i] = h->h_delta[q];
+  }
+  const double delta = h->h_delta[0];
+  h->dsub.upload(hdsub, st);
   std::vector<double> hs_shift(N);
   for (int i = 0; i < N; ++i) hs_shift[i] = h->opt.s_rel * std::sqrt(hctn2[i]);
   sdev.upload(hs_shift, st);
   h->eqs.alloc(h->total_local);
   Bst.alloc(h->fac_elems);  // prep always writes B = C~_ii + s I
-  lsq::launch_prep(plan, delta, sdev.p, Cst.p, h->eqs.p, Ctst.p, Bst.p, st);
+  lsq::launch_prep(plan, h->dsub.p, sdev.p, Cst.p, h->eqs.p, Ctst.p, Bst.p, st);
   check_launch("prep");
   DevBuf<double> dinv, Bidiag, idiag;
   DevBuf<int> status;
@@ -743,7 +637,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     lam.alloc((size_t)N * kw); lam.zero(st);
     nconv.alloc(N); steps.alloc(N); est.alloc(N);
     lsq::EigArgs ea{};
-    ea.P = plan; ea.Bfac = Bst.p; ea.Bidiag = Bidiag.p; ea.Ct = Ctst.p; ea.delta = delta;
+    ea.P = plan; ea.Bfac = Bst.p; ea.Bidiag = Bidiag.p; ea.Ct = Ctst.p; ea.delta = h->dsub.p;
     ea.kwant_cap = kw; ea.Kmax = K; ea.keep = keep; ea.maxit = h->opt.eig_maxit; ea.tol = h->opt.eig_tol;
     ea.V = V.p; ea.V2 = V2.p; ea.vstride = vs; ea.H = H.p; ea.S = S.p; ea.vec = vec.p; ea.lam = lam.p;
     ea.nconv = nconv.p; ea.steps = steps.p; ea.status = est.p;
@@ -763,23 +657,30 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
       }
     }
     // threshold 1/tau (Lemma 2.4 / eq. (3.6)); tau <= 0: max_i lambda_{i, nev_max+1}
-    double thr;
-    if (h->opt.tau > 0) {
-      thr = 1.0 / h->opt.tau;
-    } else {
-      thr = 0.0;
-      for (int i = 0; i < N; ++i) {
-        const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
-        if (ni > h->opt.nev_max) thr = std::max(thr, h->h_lam[(size_t)i * kw + h->opt.nev_max]);
+    // (per independent problem when batched)
+    h->h_thr.assign(h->nprob, 0.0);
+    double thr_max = 0.0;
+    for (int q = 0; q < h->nprob; ++q) {
+      double thr = 0.0;
+      if (h->opt.tau > 0) {
+        thr = 1.0 / h->opt.tau;
+      } else {
+        for (int i = h->h_N_off[q]; i < h->h_N_off[q + 1]; ++i) {
+          const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
+          if (ni > h->opt.nev_max) thr = std::max(thr, h->h_lam[(size_t)i * kw + h->opt.nev_max]);
+        }
       }
+      h->h_thr[q] = thr;
+      thr_max = std::max(thr_max, thr);
     }
-    h->sinfo.tau_used = thr > 0 ? 1.0 / thr : INFINITY;
+    h->sinfo.tau_used = thr_max > 0 ? 1.0 / thr_max : INFINITY;
     std::vector<int32_t> hcoff(N + 1, 0);
     std::vector<int64_t> hzoff(N + 1, 0), hwoff(N + 1, 0);
     int kmin = 1 << 30, kmax = 0;
     for (int i = 0; i < N; ++i) {
       const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
       const int lim = (int)std::min<int64_t>(std::min<int64_t>(kw, ni), h->opt.nev_max);
+      const double thr = h->h_thr[h->prob_of_sub[i]];
       int k = 0;
       while (k < lim && h->h_lam[(size_t)i * kw + k] > thr) ++k;
       h->h_k[i] = k;
@@ -814,24 +715,51 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
                            h->Z.p, W.p, hs.xi_off[N], xi_sub.p, st);
       pi.upload(hs.pair_i, st); pj.upload(hs.pair_j, st); poff.upload(hs.pair_off, st);
       ppi.upload(hs.pair_pi, st); ppj.upload(hs.pair_pj, st);
-      h->n0p = (h->n0 + 31) / 32 * 32;
-      h->Xinv.alloc((size_t)h->n0p * h->n0p);
+      // C_00 in one dense block per problem, each padded to a multiple of 32
+      const int Q = h->nprob;
+      h->h_cb_base.assign(Q, 0); h->h_cb_ld.assign(Q, 0); h->h_cb_c0.assign(Q, 0); h->h_n0q.assign(Q, 0);
+      int64_t base = 0, ldmax = 0;
+      for (int q = 0; q < Q; ++q) {
+        h->h_cb_c0[q] = hcoff[h->h_N_off[q]];
+        h->h_n0q[q] = hcoff[h->h_N_off[q + 1]] - hcoff[h->h_N_off[q]];
+        h->h_cb_ld[q] = (h->h_n0q[q] + 31) / 32 * 32;
+        h->h_cb_base[q] = base;
+        base += h->h_cb_ld[q] * h->h_cb_ld[q];
+        ldmax = std::max(ldmax, h->h_cb_ld[q]);
+      }
+      h->xinv_elems = base;
+      h->n0p = h->h_cb_ld[0];
+      h->cb_prob_of_sub.upload(h->prob_of_sub, st);
+      h->cb_base.upload(h->h_cb_base, st);
+      h->cb_ld.upload(h->h_cb_ld, st);
+      h->cb_c0.upload(h->h_cb_c0, st);
+      h->Xinv.alloc((size_t)base);
       h->Xinv.zero(st);
-      k_set_diag<<<32, 256, 0, st>>>(h->Xinv.p, h->n0p, h->n0, h->n0p, 1.0);
+      for (int q = 0; q < Q; ++q)
+        if (h->h_cb_ld[q] > h->h_n0q[q])
+          k_set_diag<<<32, 256, 0, st>>>(h->Xinv.p + h->h_cb_base[q], h->h_cb_ld[q], h->h_n0q[q], h->h_cb_ld[q], 1.0);
+      const lsq::CoarseBlocks cb{h->cb_prob_of_sub.p, h->cb_base.p, h->cb_ld.p, h->cb_c0.p};
       lsq::launch_coarse_pairs((int)hs.pair_i.size(), pi.p, pj.p, poff.p, ppi.p, ppj.p, h->coff.p, woff.p, h->zoff.p,
-                               h->nI.p, W.p, h->Z.p, delta, h->n0p, h->Xinv.p, st);
+                               h->nI.p, W.p, h->Z.p, h->dsub.p, cb, h->Xinv.p, st);
       check_launch("coarse operator");
       W.release();
       DevBuf<double> Y, dinvc;
-      Y.alloc((size_t)h->n0p * h->n0p);
-      dinvc.alloc((size_t)(h->n0p / 32) * 1024);
-      CK(cudaMemsetAsync(status.p, 0, sizeof(int), st));
-      lsq::dense_spd_inverse(h->n0p, h->Xinv.p, Y.p, dinvc.p, status.p, st);
-      int cst = 0;
-      CK(cudaMemcpyAsync(&cst, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      Y.alloc((size_t)ldmax * ldmax);
+      dinvc.alloc((size_t)(ldmax / 32) * 1024);
+      DevBuf<int> cstat;
+      cstat.alloc(Q);
+      cstat.zero(st);
+      for (int q = 0; q < Q; ++q)
+        if (h->h_n0q[q] > 0)
+          lsq::dense_spd_inverse(h->h_cb_ld[q], h->Xinv.p + h->h_cb_base[q], Y.p, dinvc.p, cstat.p + q, st);
+      std::vector<int> hcst(Q);
+      CK(cudaMemcpyAsync(hcst.data(), cstat.p, sizeof(int) * Q, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       check_launch("coarse factorization");
-      if (cst) throw LsError(LS_ERR_FACTOR, "Cholesky of C_00 failed at row " + std::to_string(cst - 1));
+      for (int q = 0; q < Q; ++q)
+        if (hcst[q])
+          throw LsError(LS_ERR_FACTOR, "Cholesky of C_00 failed at row " + std::to_string(hcst[q] - 1) +
+                                           (Q > 1 ? " of problem " + std::to_string(q) : std::string()));
     }
     h->sinfo.t_eig = now_s() - te0;
   } else {
@@ -869,6 +797,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   if (h->opt.time_kernels)
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
   std::memset(h->pin, 0, sizeof(double) * lsq::S_NSLOT);
+  block_plan(h);
   CK(cudaStreamSynchronize(st));
   h->sinfo.t_setup = now_s() - t_begin;
   h->sinfo.bad_subdomain = -1;
@@ -897,9 +826,11 @@ void ls_default_options(ls_options* o) {
 
 const char* ls_last_error(void) { return g_err.c_str(); }
 
-ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
-                   int32_t nparts, const int32_t* part, int overlap, const ls_options* opt, void* stream,
-                   ls_handle** out) {
+namespace {
+
+ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off, int64_t m, int64_t n,
+                      const int64_t* row_ptr, const int32_t* col, const double* val, int32_t nparts,
+                      const int32_t* part, int overlap, const ls_options* opt, void* stream, ls_handle** out) {
   if (out) *out = nullptr;
   return guarded([&]() -> ls_status {
     if (!out || !row_ptr || !part || (!col && m > 0) || (!val && m > 0))
@@ -922,6 +853,14 @@ ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* 
       h->own_stream = true;
     }
     h->m = m; h->n = n; h->N = nparts;
+    h->nprob = nprob;
+    if (m_off && n_off) {
+      h->h_m_off.assign(m_off, m_off + nprob + 1);
+      h->h_n_off.assign(n_off, n_off + nprob + 1);
+    } else {
+      h->h_m_off = {0, m};
+      h->h_n_off = {0, n};
+    }
     h->coarse = h->opt.coarse != 0 && h->opt.nev_max > 0;
     h->sinfo.bad_subdomain = -1;
     try {
@@ -935,11 +874,32 @@ ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* 
   });
 }
 
+}  // namespace
+
+ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   int32_t nparts, const int32_t* part, int overlap, const ls_options* opt, void* stream,
+                   ls_handle** out) {
+  return setup_entry(1, nullptr, nullptr, m, n, row_ptr, col, val, nparts, part, overlap, opt, stream, out);
+}
+
+ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n_off, const int64_t* row_ptr,
+                           const int32_t* col, const double* val, int32_t nparts, const int32_t* part, int overlap,
+                           const ls_options* opt, void* stream, ls_handle** out) {
+  if (nprob < 1 || !m_off || !n_off) {
+    if (out) *out = nullptr;
+    g_err = "nprob must be positive and m_off, n_off non-null";
+    return LS_ERR_INVALID;
+  }
+  return setup_entry(nprob, m_off, n_off, m_off[nprob], n_off[nprob], row_ptr, col, val, nparts, part, overlap, opt,
+                     stream, out);
+}
+
 ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x, ls_info* info) {
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
     if (!(rtol > 0) && h->opt.fixed_iters <= 0) throw LsError(LS_ERR_INVALID, "rtol must be positive");
     CK(cudaSetDevice(h->dev));
+    if (nrhs > 1 || h->nprob > 1) return block_solve(h, b, nrhs, rtol, x, info);
     ls_status last = LS_OK;
     for (int k = 0; k < nrhs; ++k) {
       // b' = P b for the row-reordered device matrix
@@ -958,6 +918,7 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
                       double* grad_b, double* grad_vals, ls_info* info) {
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || !grad_x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
+    if (h->nprob > 1) throw LsError(LS_ERR_UNSUPPORTED, "ls_backward on a batched handle");
     CK(cudaSetDevice(h->dev));
     cudaStream_t st = h->st;
     ls_status last = LS_OK;
@@ -1022,6 +983,7 @@ ls_status ls_handle_info(const ls_handle* h, ls_info* info) {
 ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int which) {
   return guarded([&]() -> ls_status {
     if (!h || !r || !z || which < 0 || which > 2) throw LsError(LS_ERR_INVALID, "bad arguments");
+    if (h->nprob > 1) throw LsError(LS_ERR_UNSUPPORTED, "single-vector preconditioner apply on a batched handle");
     CK(cudaSetDevice(h->dev));
     CK(cudaMemcpyAsync(h->tv.p, r, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     if (which == 2) {
@@ -1082,6 +1044,17 @@ ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap) 
       for (int s = 0; s < N; ++s) zel += (int64_t)(h->h_k.empty() ? 0 : h->h_k[s]) * h->h_nI[s];
       o[0] = h->fac_elems; o[1] = h->total_local; o[2] = h->total_blocks; o[3] = zel;
       o[4] = h->n0; o[5] = h->n0p; o[6] = h->nnz; o[7] = h->prec;
+      return LS_OK;
+    }
+    if (kind == LS_Q_BATCH) {
+      const int64_t k = (int64_t)h->blk.h_its.size();
+      if (k == 0) throw LsError(LS_ERR_INVALID, "no multi right-hand-side solve has run");
+      need(2 * k);
+      double* o = (double*)out;
+      for (int64_t a = 0; a < k; ++a) {
+        o[a] = h->blk.h_its[a];
+        o[k + a] = h->blk.h_rel[a];
+      }
       return LS_OK;
     }
     if (kind == LS_Q_EIGSTEPS) {

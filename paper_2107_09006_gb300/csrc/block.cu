@@ -1,0 +1,373 @@
+// Multi right-hand-side PCG on the normal equations: R <= 32 right-hand sides of every
+// problem of the handle advance together, each (problem, right-hand side) pair with its
+// own CG scalars (the same recurrences as the single-vector path: plain PCG for FP64
+// local factors, the flexible form for FP32/BF16 factors), its own stopping test and
+// its own true-residual check.  A pair that meets its test is frozen (alpha = 0) while
+// the others continue; the iteration is one CUDA graph replayed until every pair has
+// passed.  Every kernel serves all pairs: the factor tiles, A and the coarse basis are
+// read once per iteration for all R right-hand sides.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+using namespace lsi;
+
+namespace {
+
+constexpr int kChunkCols = 256;
+
+lsq::BChunks chunks(const ls_handle* h) {
+  return lsq::BChunks{h->blk.nchunks, h->blk.chunk_start.p, h->blk.chunk_prob.p};
+}
+
+lsq::BScal scal(ls_handle* h) {
+  const int64_t P = (int64_t)h->nprob * 32;
+  double* s = h->blk.sc.p;
+  return lsq::BScal{s, s + P, s + 2 * P, s + 3 * P, s + 4 * P, s + 5 * P, s + 6 * P, s + 7 * P,
+                    h->blk.act.p, h->blk.its.p, h->blk.stat.p};
+}
+
+int arith_bytes(int prec) { return prec == LS_PREC_F64 ? 8 : 4; }
+int fac_bytes(int prec) { return prec == LS_PREC_F64 ? 8 : prec == LS_PREC_F32 ? 4 : 2; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void ensure_buffers(ls_handle* h, int R) {
+  BlockState& B = h->blk;
+  if (B.R >= R) return;
+  if (B.gexec) {
+    cudaGraphExecDestroy(B.gexec);
+    B.gexec = nullptr;
+  }
+  const size_t n = (size_t)h->n * R, m = (size_t)h->m * R;
+  B.X.alloc(n); B.Rv.alloc(n); B.Rold.alloc(n); B.Z.alloc(n); B.P.alloc(n); B.W.alloc(n);
+  B.Q.alloc(m); B.B.alloc(m); B.Bu.alloc(m);
+  B.Y.alloc((size_t)h->total_local * R);
+  B.R0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
+  B.Y0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
+  B.R = R;
+}
+
+// z = M^{-1} r for all pairs, with the partials of r.z (and rold.z when flexible).
+void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool flex, bool timed) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  lsq::BLocalArgs a{};
+  a.N = h->N; a.order = B.order.p; a.qctr = B.qctr.p;
+  a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
+  a.blk_off = h->blk_off.p; a.blk_tf = h->blk_tf.p; a.blk_poff = h->blk_poff.p;
+  a.fac = h->prec == LS_PREC_F64 ? (const void*)h->L64.p
+        : h->prec == LS_PREC_F32 ? (const void*)h->L32.p : (const void*)h->L16.p;
+  a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
+  a.Rv = Rin; a.Y = B.Y.p; a.R = R; a.Vg = B.Vg.p; a.ring = B.ring;
+  a.err = h->scal.p + lsq::S_ERR;
+  lsq::launch_b_local(h->prec, a, B.local_grid, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  const bool coarse = h->coarse && h->n0 > 0;
+  if (coarse) {
+    lsq::launch_b_restrict(h->N, R, h->int_off.p, h->int_glob.p, h->zoff.p, h->coff.p, h->Z.p, Rin, B.R0.p, st);
+    const lsq::CoarseBlocks cb{h->cb_prob_of_sub.p, h->cb_base.p, h->cb_ld.p, h->cb_c0.p};
+    lsq::launch_b_coarse(B.nct, R, B.ct_prob.p, B.ct_row.p, cb, B.n0q.p, h->Xinv.p, B.R0.p, B.Y0.p, st);
+  }
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  lsq::BScatterArgs s{};
+  s.R = R;
+  s.Rp = 1;
+  while (s.Rp < R) s.Rp <<= 1;
+  s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.Y = B.Y.p;
+  s.coarse = coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p; s.coff = h->coff.p;
+  s.nI = h->nI.p; s.Z = h->Z.p; s.Y0 = B.Y0.p;
+  s.Rv = Rin; s.Rold = flex ? B.Rold.p : nullptr; s.Zout = Zout;
+  s.part1 = B.parts.p; s.part2 = B.parts.p + (size_t)B.nchunks * 32;
+  lsq::launch_b_scatter(chunks(h), s, st);
+}
+
+int precond_launches(const ls_handle* h) { return 2 + ((h->coarse && h->n0 > 0) ? 2 : 0); }
+
+void iteration_block(ls_handle* h, int R, bool flex) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  const bool timed = h->opt.time_kernels != 0;
+  const lsq::BScal sc = scal(h);
+  const lsq::BChunks ch = chunks(h);
+  double* part2 = B.parts.p + (size_t)B.nchunks * 32;
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
+  lsq::launch_b_spmm_csr(csr(h), B.P.p, B.Q.p, R, st);
+  lsq::launch_b_spmm_csc(ch, csc(h), B.Q.p, B.W.p, R, B.P.p, B.parts.p, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinAlpha, 0, st);
+  lsq::launch_b_update(ch, R, sc.alpha, B.P.p, B.W.p, B.X.p, B.Rv.p, flex ? B.Rold.p : nullptr, B.parts.p, st);
+  CK(cudaMemsetAsync(B.stat.p, 0, sizeof(int), st));
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinRR, 0, st);
+  precond_block(h, R, B.Rv.p, B.Z.p, flex, timed);
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, flex ? part2 : nullptr, R, sc, lsq::kFinBeta, flex ? 1 : 0,
+                       st);
+  lsq::launch_b_pupdate(ch, R, sc.beta, B.Z.p, B.P.p, 0, st);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[5], st, cudaEventRecordExternal));
+  CK(cudaMemcpyAsync(B.pin, B.stat.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(B.pin + 2, h->scal.p + lsq::S_ERR, sizeof(double), cudaMemcpyDeviceToHost, st));
+}
+
+int iteration_launches(const ls_handle* h) { return 8 + precond_launches(h); }
+
+template <class T>
+std::vector<T> fetch(const T* p, size_t n, cudaStream_t st) {
+  std::vector<T> v(n);
+  if (n) CK(cudaMemcpyAsync(v.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return v;
+}
+
+// tt = ||A^T (B - A X)||^2 per pair (W receives the residual vectors).
+std::vector<double> true_residual_block(ls_handle* h, int R, int* launches) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  const lsq::BScal sc = scal(h);
+  lsq::launch_b_spmm_csr(csr(h), B.X.p, B.Q.p, R, st);
+  lsq::launch_b_sub((int64_t)h->m * R, B.B.p, B.Q.p, st);
+  lsq::launch_b_spmm_csc(chunks(h), csc(h), B.Q.p, B.W.p, R, nullptr, B.parts.p, st);
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinTT, 0, st);
+  *launches += 4;
+  return fetch(sc.tt, (size_t)h->nprob * R, st);
+}
+
+}  // namespace
+
+namespace lsi {
+
+void block_plan(ls_handle* h) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  // chunks
+  std::vector<int64_t> start;
+  std::vector<int32_t> prob;
+  B.h_pc_off.assign(h->nprob + 1, 0);
+  for (int q = 0; q < h->nprob; ++q) {
+    B.h_pc_off[q] = (int64_t)start.size();
+    for (int64_t j = h->h_n_off[q]; j < h->h_n_off[q + 1]; j += kChunkCols) {
+      start.push_back(j);
+      prob.push_back(q);
+    }
+  }
+  B.h_pc_off[h->nprob] = (int64_t)start.size();
+  B.nchunks = (int64_t)start.size();
+  start.push_back(h->n);
+  B.chunk_start.upload(start, st);
+  B.chunk_prob.upload(prob, st);
+  B.pc_off.upload(B.h_pc_off, st);
+  B.parts.alloc((size_t)B.nchunks * 32 * 2);
+  B.sc.alloc((size_t)h->nprob * 32 * 8);
+  B.sc.zero(st);
+  B.act.alloc((size_t)h->nprob * 32);
+  B.its.alloc((size_t)h->nprob * 32);
+  B.stat.alloc(2);
+  B.qctr.alloc(1);
+  if (!B.pin) CK(cudaMallocHost(&B.pin, 4 * sizeof(int)));
+  // work order of the persistent local solve: subdomains by decreasing size
+  std::vector<int32_t> order(h->N);
+  for (int i = 0; i < h->N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return h->h_om_off[a + 1] - h->h_om_off[a] > h->h_om_off[b + 1] - h->h_om_off[b];
+  });
+  B.order.upload(order, st);
+  B.ring = h->wmax;
+  int optin = 0, sms = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+  const size_t need = lsq::block_local_smem(fac_bytes(h->prec), arith_bytes(h->prec), B.ring);
+  B.local_ok = need <= (size_t)optin;
+  if (B.local_ok) {
+    const int occ = lsq::block_local_occupancy(h->prec, B.ring);
+    B.local_grid = std::max(1, std::min(h->N, sms * std::max(occ, 1)));
+    B.Vg.alloc((size_t)h->total_blocks * 1024 * arith_bytes(h->prec));
+  }
+  // coarse tiles (problem, 32-row tile)
+  std::vector<int32_t> cp, cr, n0q(h->nprob, 0);
+  for (int q = 0; q < h->nprob; ++q) {
+    n0q[q] = h->h_n0q.empty() ? 0 : h->h_n0q[q];
+    for (int t = 0; t < (n0q[q] + 31) / 32; ++t) {
+      cp.push_back(q);
+      cr.push_back(t);
+    }
+  }
+  B.nct = (int)cp.size();
+  B.ct_prob.upload(cp, st);
+  B.ct_row.upload(cr, st);
+  B.n0q.upload(n0q, st);
+  CK(cudaStreamSynchronize(st));
+  check_launch("block plan");
+}
+
+ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double* x, ls_info* info) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  if (R < 1 || R > 32) throw LsError(LS_ERR_UNSUPPORTED, "the multi right-hand-side path takes 1 to 32 right-hand sides");
+  if (!B.local_ok)
+    throw LsError(LS_ERR_UNSUPPORTED, "the widest local factor block row (" + std::to_string(B.ring) +
+                                          " tiles) does not fit the multi right-hand-side local solve");
+  const double t0 = now_s();
+  const bool flex = h->prec != LS_PREC_F64;
+  const int NP = h->nprob * R;
+  ensure_buffers(h, R);
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
+  const lsq::BScal sc = scal(h);
+  const lsq::BChunks ch = chunks(h);
+  // B = P b (interleaved), R = G = A^T B, gg = ||G||^2
+  const double* bsrc = b;
+  if (!is_device_ptr(b)) {
+    CK(cudaMemcpyAsync(B.Bu.p, b, sizeof(double) * h->m * R, cudaMemcpyHostToDevice, st));
+    bsrc = B.Bu.p;
+  }
+  lsq::launch_b_load_rows(h->m, R, h->perm.p, bsrc, B.B.p, st);
+  lsq::launch_b_spmm_csc(ch, csc(h), B.B.p, B.Rv.p, R, nullptr, B.parts.p, st);
+  CK(cudaMemsetAsync(B.act.p, 0, sizeof(int) * NP, st));
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinGG, 0, st);
+  launches += 3;
+  std::vector<double> gg = fetch(sc.gg, NP, st);
+  const int fixed = h->opt.fixed_iters;
+  std::vector<double> thr2(NP);
+  std::vector<int> act(NP);
+  int nact = 0;
+  for (int i = 0; i < NP; ++i) {
+    if (!std::isfinite(gg[i])) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
+    act[i] = gg[i] > 0.0 ? 1 : 0;
+    thr2[i] = fixed > 0 ? -1.0 : rtol * rtol * gg[i];
+    nact += act[i];
+  }
+  CK(cudaMemcpyAsync(sc.thr2, thr2.data(), sizeof(double) * NP, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sc.act, act.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(sc.its, 0, sizeof(int) * NP, st));
+  CK(cudaMemsetAsync(B.X.p, 0, sizeof(double) * h->n * R, st));
+  CK(cudaMemsetAsync(B.stat.p, 0, sizeof(int) * 2, st));
+  CK(cudaMemsetAsync(h->scal.p + lsq::S_ERR, 0, sizeof(double), st));
+  auto restart = [&]() {
+    precond_block(h, R, B.Rv.p, B.Z.p, false, false);
+    lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinBeta0, 0, st);
+    lsq::launch_b_pupdate(ch, R, sc.beta, B.Z.p, B.P.p, 1, st);
+    launches += precond_launches(h) + 2;
+    inf.local_launches += 1;
+  };
+  const int maxit = fixed > 0 ? fixed : h->opt.maxit;
+  bool converged = nact == 0;
+  int it = 0, restarts = 0;
+  std::vector<double> tt;
+  if (!converged) {
+    restart();
+    check_launch("initial block preconditioner apply");
+  }
+  const bool timed = h->opt.time_kernels != 0;
+  bool graph_this = h->opt.use_graph != 0;
+  while (!converged && it < maxit) {
+    if (graph_this) {
+      if (!B.gexec || B.gR != R) {
+        if (B.gexec) cudaGraphExecDestroy(B.gexec);
+        B.gexec = nullptr;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        iteration_block(h, R, flex);
+        CK(cudaStreamEndCapture(st, &g));
+        cudaError_t e = cudaGraphInstantiate(&B.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          B.gexec = nullptr;
+          cudaGetLastError();
+          graph_this = false;
+          continue;
+        }
+        B.gR = R;
+      }
+      CK(cudaGraphLaunch(B.gexec, st));
+    } else {
+      iteration_block(h, R, flex);
+    }
+    CK(cudaStreamSynchronize(st));
+    check_launch("block CG iteration");
+    ++it;
+    launches += iteration_launches(h);
+    inf.local_launches += 1;
+    if (timed) {
+      float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
+      CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[1]));
+      CK(cudaEventElapsedTime(&tb, h->ev[2], h->ev[3]));
+      CK(cudaEventElapsedTime(&tc, h->ev[3], h->ev[4]));
+      CK(cudaEventElapsedTime(&td, h->ev[0], h->ev[5]));
+      inf.ms_spmv += ta; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
+    }
+    const double* perr = reinterpret_cast<const double*>(B.pin + 2);
+    if (*perr != 0.0)
+      throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the block local-solve kernel gave up at iteration " +
+                                               std::to_string(it));
+    if (B.pin[1] != 0)
+      throw LsError(LS_ERR_NONFINITE, "block CG breakdown (non-finite scalar or non-positive p.Cp) at iteration " +
+                                          std::to_string(it));
+    if (fixed > 0) continue;
+    if (B.pin[0] == 0) {
+      tt = true_residual_block(h, R, &launches);
+      int fail = 0;
+      for (int i = 0; i < NP; ++i) {
+        act[i] = (gg[i] > 0.0 && tt[i] > thr2[i]) ? 1 : 0;
+        fail += act[i];
+      }
+      if (fail == 0) {
+        converged = true;
+        break;
+      }
+      CK(cudaMemcpyAsync(sc.act, act.data(), sizeof(int) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(B.Rv.p, B.W.p, sizeof(double) * h->n * R, cudaMemcpyDeviceToDevice, st));
+      ++restarts;
+      restart();
+    }
+  }
+  if (tt.empty() || !converged) tt = true_residual_block(h, R, &launches);
+  // x (caller's column-major layout)
+  if (is_device_ptr(x)) {
+    lsq::launch_b_store_cols(h->n, R, B.X.p, x, st);
+  } else {
+    lsq::launch_b_store_cols(h->n, R, B.X.p, B.Bu.p, st);
+    CK(cudaMemcpyAsync(x, B.Bu.p, sizeof(double) * h->n * R, cudaMemcpyDeviceToHost, st));
+  }
+  launches += 1;
+  std::vector<int> its = fetch(sc.its, NP, st);
+  std::vector<double> rr = fetch(sc.rr, NP, st);
+  check_launch("block solve");
+  B.h_its.assign(its.begin(), its.end());
+  B.h_rel.assign(NP, 0.0);
+  double worst = 0.0, worst_rec = 0.0;
+  for (int i = 0; i < NP; ++i) {
+    const double g = gg[i] > 0.0 ? std::sqrt(gg[i]) : 1.0;
+    B.h_rel[i] = gg[i] > 0.0 ? std::sqrt(std::max(tt[i], 0.0)) / g : 0.0;
+    worst = std::max(worst, B.h_rel[i]);
+    if (gg[i] > 0.0) worst_rec = std::max(worst_rec, std::sqrt(std::max(rr[i], 0.0)) / g);
+    inf.iters = std::max(inf.iters, its[i]);
+  }
+  if (fixed > 0) inf.iters = it;
+  inf.restarts = restarts;
+  inf.relres_true = worst;
+  inf.relres_recursive = worst_rec;
+  inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
+  inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
+  inf.eig_steps_max = h->sinfo.eig_steps_max;
+  inf.launches = launches;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  inf.t_solve = now_s() - t0;
+  if (info) *info = inf;
+  if (!converged && fixed <= 0)
+    throw LsError(LS_ERR_NOT_CONVERGED, "maximum number of iterations reached, worst true relative residual " +
+                                            std::to_string(worst));
+  return LS_OK;
+}
+
+}  // namespace lsi

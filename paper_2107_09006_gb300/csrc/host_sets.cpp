@@ -113,6 +113,41 @@ std::string validate_inputs(int64_t m, int64_t n, const int64_t* row_ptr, const 
   return std::string();
 }
 
+std::string validate_batch(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int N,
+                           const int32_t* part, int nprob, const int64_t* m_off, const int64_t* n_off,
+                           std::vector<int32_t>& N_off, std::vector<int32_t>& prob_of_sub) {
+  if (nprob < 1) return "nprob must be positive";
+  if (m_off[0] != 0 || n_off[0] != 0 || m_off[nprob] != m || n_off[nprob] != n)
+    return "problem offsets must start at 0 and end at m and n";
+  for (int q = 0; q < nprob; ++q) {
+    const int64_t mq = m_off[q + 1] - m_off[q], nq = n_off[q + 1] - n_off[q];
+    if (nq < 1 || mq < nq) return "problem " + std::to_string(q) + " needs m_q >= n_q >= 1";
+    for (int64_t r = m_off[q]; r < m_off[q + 1]; ++r)
+      for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+        if (col[e] < n_off[q] || col[e] >= n_off[q + 1])
+          return "row " + std::to_string(r) + " of problem " + std::to_string(q) + " has a column outside it";
+  }
+  N_off.assign(nprob + 1, 0);
+  prob_of_sub.assign(N, -1);
+  for (int q = 0; q < nprob; ++q) {
+    int lo = INT32_MAX, hi = -1;
+    for (int64_t j = n_off[q]; j < n_off[q + 1]; ++j) {
+      lo = std::min(lo, part[j]);
+      hi = std::max(hi, part[j]);
+    }
+    if (lo != N_off[q])
+      return "subdomain ids of problem " + std::to_string(q) + " must start at " + std::to_string(N_off[q]);
+    N_off[q + 1] = hi + 1;
+    for (int i = lo; i <= hi; ++i) prob_of_sub[i] = q;
+  }
+  if (N_off[nprob] != N) return "subdomain ids must run through 0 .. nparts-1 in problem order";
+  for (int64_t j = 0; j < n; ++j) {
+    const int q = prob_of_sub[part[j]];
+    if (j < n_off[q] || j >= n_off[q + 1]) return "subdomain " + std::to_string(part[j]) + " spans two problems";
+  }
+  return std::string();
+}
+
 std::string build_host_sets(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
                             int N, const int32_t* part, bool with_pairs, HostSets& hs) {
   if (m < 1 || n < 1) return "m and n must be positive";

@@ -78,6 +78,14 @@ void build_sell(int64_t nrows, const int64_t* ptr, const int32_t* idx, const dou
 std::string validate_inputs(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int N,
                             const int32_t* part);
 
+// Batched problems: checks that A is block diagonal over the nprob problems (rows
+// [m_off[q], m_off[q+1]) touch only columns [n_off[q], n_off[q+1])), that every problem
+// has m_q >= n_q >= 1, and that the subdomain ids of problem q form one range
+// [N_off[q], N_off[q+1]) in problem order; fills N_off and prob_of_sub.  "" if valid.
+std::string validate_batch(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, int N,
+                           const int32_t* part, int nprob, const int64_t* m_off, const int64_t* n_off,
+                           std::vector<int32_t>& N_off, std::vector<int32_t>& prob_of_sub);
+
 // Row order by first stored column (stable; empty rows last): perm[new] = old row.
 // Rows of a least-squares problem may be permuted freely; this order keeps the
 // vector entries that neighbouring rows and columns touch close in memory.

@@ -86,10 +86,11 @@ __global__ void __launch_bounds__(kThreads) k_norms(BandPlan P, const double* __
 
 // C_ii += delta I; eqs = diag^{-1/2}; C_ii <- diag(eqs) C_ii diag(eqs); B = C~_ii + s_i I.
 // Padding rows (k >= n_i) become identity rows in both storages.
-__global__ void __launch_bounds__(kThreads) k_prep(BandPlan P, double delta, const double* __restrict__ s,
+__global__ void __launch_bounds__(kThreads) k_prep(BandPlan P, const double* __restrict__ dsub, const double* __restrict__ s,
                                                    double* __restrict__ C, double* __restrict__ eqs,
                                                    const double* __restrict__ Ct, double* __restrict__ B) {
   const int i = blockIdx.x;
+  const double delta = dsub[i];
   const int64_t o0 = P.om_off[i];
   const int ni = (int)(P.om_off[i + 1] - o0);
   const int64_t b0 = P.blk_off[i];
@@ -204,9 +205,9 @@ void launch_norms(const BandPlan& P, const double* Cst, const double* Ctst, doub
   k_norms<<<P.N, kThreads, 0, st>>>(P, Cst, Ctst, cn2, ctn2);
 }
 
-void launch_prep(const BandPlan& P, double delta, const double* s, double* Cst, double* eqs,
+void launch_prep(const BandPlan& P, const double* dsub, const double* s, double* Cst, double* eqs,
                  const double* Ctst, double* Bst, cudaStream_t st) {
-  k_prep<<<P.N, kThreads, 0, st>>>(P, delta, s, Cst, eqs, Ctst, Bst);
+  k_prep<<<P.N, kThreads, 0, st>>>(P, dsub, s, Cst, eqs, Ctst, Bst);
 }
 
 void launch_band_cholesky(const BandPlan& P, double* F, double* idiag, double* dinv, int* status,

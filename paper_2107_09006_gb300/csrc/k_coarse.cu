@@ -41,12 +41,16 @@ __global__ void __launch_bounds__(kThreads) k_coarse_pairs(const int32_t* __rest
                                                            const int32_t* __restrict__ ppj, const int32_t* __restrict__ coff,
                                                            const int64_t* __restrict__ woff, const int64_t* __restrict__ zoff,
                                                            const int32_t* __restrict__ nI, const double* __restrict__ W,
-                                                           const double* __restrict__ Z, double delta, int64_t ld,
-                                                           double* __restrict__ C00) {
+                                                           const double* __restrict__ Z, const double* __restrict__ dsub,
+                                                           CoarseBlocks cb, double* __restrict__ C00) {
   const int p = blockIdx.x;
   const int i = pi[p], j = pj[p];
-  const int ci = coff[i], ki = coff[i + 1] - ci;
-  const int cj = coff[j], kj = coff[j + 1] - cj;
+  const int q = cb.prob_of_sub[i];  // i and j belong to the same problem
+  const int64_t ld = cb.ld[q];
+  double* Cq = C00 + cb.base[q];
+  const int ci = coff[i] - cb.c0[q], ki = coff[i + 1] - coff[i];
+  const int cj = coff[j] - cb.c0[q], kj = coff[j + 1] - coff[j];
+  const double delta = dsub[i];
   if (ki == 0 || kj == 0) return;
   const double* Wi = W + woff[i];
   const double* Wj = W + woff[j];
@@ -61,8 +65,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_pairs(const int32_t* __rest
       for (int64_t q = 0; q < n; ++q) zz += Zi[t * n + q] * Zi[u * n + q];
       acc += delta * zz;
     }
-    C00[(int64_t)(ci + t) * ld + cj + u] = acc;
-    if (i != j) C00[(int64_t)(cj + u) * ld + ci + t] = acc;
+    Cq[(int64_t)(ci + t) * ld + cj + u] = acc;
+    if (i != j) Cq[(int64_t)(cj + u) * ld + ci + t] = acc;
   }
 }
 
@@ -186,10 +190,10 @@ void launch_coarse_w(int N, const int64_t* xi_off, const int32_t* xi, const int3
 
 void launch_coarse_pairs(int npairs, const int32_t* pi, const int32_t* pj, const int64_t* poff, const int32_t* ppi,
                          const int32_t* ppj, const int32_t* coff, const int64_t* woff, const int64_t* zoff,
-                         const int32_t* nI, const double* W, const double* Z, double delta, int64_t n0,
-                         double* C00, cudaStream_t st) {
+                         const int32_t* nI, const double* W, const double* Z, const double* dsub,
+                         const CoarseBlocks& cb, double* C00, cudaStream_t st) {
   if (npairs <= 0) return;
-  k_coarse_pairs<<<npairs, kThreads, 0, st>>>(pi, pj, poff, ppi, ppj, coff, woff, zoff, nI, W, Z, delta, n0, C00);
+  k_coarse_pairs<<<npairs, kThreads, 0, st>>>(pi, pj, poff, ppi, ppj, coff, woff, zoff, nI, W, Z, dsub, cb, C00);
 }
 
 // A (n x n, n a multiple of 32) is replaced by A^{-1}; Y is an n x n scratch; dinv is

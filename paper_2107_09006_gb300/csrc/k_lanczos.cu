@@ -54,7 +54,7 @@ __device__ void apply_T(const EigArgs& a, BandRef B, const uint8_t* isint, int n
   band_symv<double>(a.Ct, B, s.x1, s.x2);
   for (int k = threadIdx.x; k < npad; k += blockDim.x) {
     const double d = (k < ni && isint[k]) ? 1.0 : 0.0;
-    s.x2[k] = d * (s.x2[k] + a.delta * s.x1[k]);
+    s.x2[k] = d * (s.x2[k] + a.delta[blockIdx.x] * s.x1[k]);
   }
   __syncthreads();
   band_forward<double, double>(a.Bfac, nullptr, a.Bidiag + (int64_t)(B.poff - a.P.blk_poff) * kT, B,

@@ -88,8 +88,9 @@ void launch_assemble(const BandPlan& P, const CsrDev& A, const CscDev& At, const
 // sum_i cn2[i] = ||C||_F^2); ctn2[i] = ||C~_ii||_F^2.
 void launch_norms(const BandPlan& P, const double* Cst, const double* Ctst, double* cn2,
                   double* ctn2, cudaStream_t st);
-// C_ii += delta I, equilibrate C_ii with eqs = diag(C_ii)^{-1/2}; B_i = C~_ii + s_i I.
-void launch_prep(const BandPlan& P, double delta, const double* s, double* Cst, double* eqs,
+// C_ii += delta_i I (dsub: one shift per subdomain, the shift of its problem),
+// equilibrate C_ii with eqs = diag(C_ii)^{-1/2}; B_i = C~_ii + s_i I.
+void launch_prep(const BandPlan& P, const double* dsub, const double* s, double* Cst, double* eqs,
                  const double* Ctst, double* Bst, cudaStream_t st);
 // In-place Cholesky of every subdomain's matrix; idiag = 1 / diag(L);
 // status[i] = 0 or 1 + the local row of the first nonpositive pivot.
@@ -119,7 +120,7 @@ struct EigArgs {
   BandPlan P;
   const double* Bfac; const double* Bidiag;  // chol(C~_ii + s I)
   const double* Ct;                          // C~_ii (lower), for D C_ii D products
-  double delta;                              // D C_ii D = D C~_ii D + delta D
+  const double* delta;                       // per subdomain: D C_ii D = D C~_ii D + delta_i D
   int kwant_cap;                             // nev_max + 1
   int Kmax; int keep;                        // basis size and restart size
   int maxit; double tol;
@@ -136,6 +137,10 @@ void launch_eigvec(const EigArgs& a, const int32_t* coff, const int64_t* zoff,
                    const int64_t* int_off, const int32_t* int_loc, double* Z, cudaStream_t st);
 
 // ---- coarse operator (k_coarse.cu) -------------------------------------------------
+// C_00 is block diagonal over independent problems: problem q's block (coarse indices
+// [c0[q], c0[q] + n0_q)) is dense row-major with leading dimension ld[q] (n0_q rounded
+// up to 32) at C00 + base[q].  One problem: base 0, ld n0p, c0 0.
+struct CoarseBlocks { const int32_t* prob_of_sub; const int64_t* base; const int64_t* ld; const int32_t* c0; };
 void launch_coarse_w(int N, const int64_t* xi_off, const int32_t* xi, const int32_t* coff,
                      const int64_t* woff, const int64_t* zoff, const int32_t* nI, const CsrDev& A,
                      const int32_t* part, const int32_t* jj_of, const double* Z, double* W,
@@ -143,11 +148,63 @@ void launch_coarse_w(int N, const int64_t* xi_off, const int32_t* xi, const int3
 void launch_coarse_pairs(int npairs, const int32_t* pi, const int32_t* pj, const int64_t* poff,
                          const int32_t* ppi, const int32_t* ppj, const int32_t* coff,
                          const int64_t* woff, const int64_t* zoff, const int32_t* nI,
-                         const double* W, const double* Z, double delta, int64_t n0, double* C00,
-                         cudaStream_t st);
+                         const double* W, const double* Z, const double* dsub, const CoarseBlocks& cb,
+                         double* C00, cudaStream_t st);
 // Dense SPD inverse through its Cholesky factor (tiles of 32; n a multiple of 32,
 // row-major, full storage): A is replaced by A^{-1}; Y (n x n) and dinv (n/32 * 1024)
 // are scratch; *status (device) receives 0 or 1 + the first failing row.
 void dense_spd_inverse(int64_t n, double* A, double* Y, double* dinv, int* status, cudaStream_t st);
+
+// ---- multi right-hand-side kernels (k_block.cu) ----------------------------------------
+// Block vectors are interleaved: entry (j, k) of an n x R block at j * R + k (R <= 32).
+// Chunks: ranges of at most 256 columns inside one problem; chunk c covers
+// [start[c], start[c+1]) of problem prob[c]; partial sums live at part[c * 32 + k].
+struct BChunks { int64_t n; const int64_t* start; const int32_t* prob; };
+// Per (problem, right-hand side) CG scalars, index q * R + k; stat[0] counts the
+// still-active pairs after a residual update, stat[1] flags a breakdown.
+struct BScal {
+  double* gg; double* thr2; double* rzold; double* pw; double* alpha; double* beta; double* rr; double* tt;
+  int* act; int* its; int* stat;
+};
+enum { kFinGG = 0, kFinAlpha = 1, kFinRR = 2, kFinBeta0 = 3, kFinBeta = 4, kFinTT = 5 };
+struct BScatterArgs {
+  int R, Rp;
+  const int64_t* map_ptr; const int64_t* map_idx; const double* Y;  // local solutions [sum n_i][R]
+  int coarse; const int32_t* part; const int32_t* jj_of; const int64_t* zoff; const int32_t* coff;
+  const int32_t* nI; const double* Z; const double* Y0;
+  const double* Rv; const double* Rold; double* Zout; double* part1; double* part2;
+};
+constexpr int kBlockRingBytes = 32768;  // shared-memory ring of factor tiles per CTA
+struct BLocalArgs {
+  int N; const int32_t* order; unsigned* qctr;  // work queue: subdomains by decreasing size
+  const int64_t* om_off; const int32_t* om_glob; const double* eqs;
+  const int64_t* blk_off; const int32_t* blk_tf; const int64_t* blk_poff;
+  const void* fac; const float* tsc;
+  const double* Rv; double* Y; int R;
+  void* Vg;  // forward-sweep spill: 32 x 32 arithmetic-precision tile per block row
+  int ring;  // tiles of the solution window kept in shared memory (>= widest block row)
+  double* err;
+};
+size_t block_local_smem(int fac_bytes, int arith_bytes, int ring);
+int block_local_occupancy(int prec, int ring);
+void launch_b_local(int prec, const BLocalArgs& a, int grid, cudaStream_t st);
+void launch_b_spmm_csr(const CsrDev& A, const double* X, double* Y, int R, cudaStream_t st);
+void launch_b_spmm_csc(const BChunks& ch, const CscDev& At, const double* Q, double* W, int R, const double* D,
+                       double* part, cudaStream_t st);
+void launch_b_update(const BChunks& ch, int R, const double* alpha, const double* P, const double* W, double* X,
+                     double* Rv, double* Rold, double* part, cudaStream_t st);
+void launch_b_pupdate(const BChunks& ch, int R, const double* beta, const double* Z, double* P, int init,
+                      cudaStream_t st);
+void launch_b_finish(int nprob, const int64_t* pc_off, const double* part, const double* part2, int R,
+                     const BScal& s, int mode, int flex, cudaStream_t st);
+void launch_b_scatter(const BChunks& ch, const BScatterArgs& a, cudaStream_t st);
+void launch_b_restrict(int N, int R, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff,
+                       const int32_t* coff, const double* Z, const double* Rv, double* R0, cudaStream_t st);
+void launch_b_coarse(int ntiles, int R, const int32_t* ct_prob, const int32_t* ct_row, const CoarseBlocks& cb,
+                     const int32_t* n0q, const double* Xinv, const double* R0, double* Y0, cudaStream_t st);
+void launch_b_load_rows(int64_t m, int R, const int32_t* perm, const double* Bu, double* Bb, cudaStream_t st);
+void launch_b_store_cols(int64_t n, int R, const double* Xb, double* Xu, cudaStream_t st);
+// b = a - b over len entries
+void launch_b_sub(int64_t len, const double* a, double* b, cudaStream_t st);
 
 }  // namespace lsq

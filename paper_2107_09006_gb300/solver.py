@@ -6,9 +6,9 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (ls_setup, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info, ls_update_values,
-               ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI,
-               LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE)
+from . import (ls_setup, ls_setup_batched, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info,
+               ls_update_values, ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA,
+               LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH)
 
 
 def _dev(a, dtype, device):
@@ -25,8 +25,11 @@ class Solver:
     use_graph).  Arrays may be numpy arrays or tensors; they are copied by setup.
     """
 
-    def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", stream=None, **options):
-        """``stream``: a torch.cuda.Stream the handle runs on (None: its own stream)."""
+    def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", stream=None, problems=None,
+                 **options):
+        """``stream``: a torch.cuda.Stream the handle runs on (None: its own stream).
+        ``problems``: None, or (m_off, n_off) row/column offsets of independent problems
+        stored block-diagonally in (row_ptr, col, val) (ls_setup_batched)."""
         self.device = torch.device(device)
         self.m, self.n = int(m), int(n)
         self.row_ptr = _dev(row_ptr, torch.int64, self.device)
@@ -35,10 +38,16 @@ class Solver:
         self.part = _dev(part, torch.int32, self.device)
         self.nparts = int(nparts)
         self.opt = ls_default_options(**options)
+        self.nprob = 1 if problems is None else len(problems[0]) - 1
         with torch.cuda.device(self.device):
             torch.cuda.synchronize(self.device)  # the inputs above were written on torch's stream
-            self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1, self.opt,
-                              stream.cuda_stream if stream is not None else None)
+            s = stream.cuda_stream if stream is not None else None
+            if problems is None:
+                self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1,
+                                  self.opt, s)
+            else:
+                self.h = ls_setup_batched(problems[0], problems[1], self.row_ptr, self.col, self.val, self.nparts,
+                                          self.part, 1, self.opt, s)
         self.stream = stream
 
     def close(self):
@@ -130,6 +139,13 @@ class Solver:
 
     def eig_steps(self) -> np.ndarray:
         return ls_query(self.h, LS_Q_EIGSTEPS, 0, np.zeros(self.nparts, np.int32))
+
+    def batch_stats(self, nrhs) -> tuple:
+        """(iterations, true relative residuals) of the last multi right-hand-side solve,
+        each of shape [nprob, nrhs]."""
+        out = ls_query(self.h, LS_Q_BATCH, 0, np.zeros(2 * self.nprob * nrhs, np.float64))
+        k = self.nprob * nrhs
+        return out[:k].reshape(self.nprob, nrhs).astype(np.int64), out[k:].reshape(self.nprob, nrhs)
 
 
 class LSSolve(torch.autograd.Function):

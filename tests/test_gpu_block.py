@@ -1,0 +1,167 @@
+"""Parity of the multi right-hand-side and batched paths with the FP64 oracle.
+
+* Several right-hand sides of one problem (96 x 96 grid, 9 subdomains, FP64 factors):
+  six fixed PCG iterations of every right-hand side against the oracle's PCG
+  (<= 1e-10 relative; same operators, different summation order), and the converged
+  solutions against the single-vector path.
+* Batched problems of different sizes (uneven bisection subdomains), each set up by
+  the oracle alone: the per-problem coarse dimensions, six fixed iterations of every
+  (problem, right-hand side) pair, and converged solves in FP64 / FP32 / BF16 factor
+  forms that meet every pair's own true-residual test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2107_09006_gb300 as L  # noqa: E402
+import oracle as O  # noqa: E402
+from workloads import make_grid_ls, block_partition, config_batch  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def grid96():
+    m, n, rp, c, v, b, _ = make_grid_ls(96, 96, 4, 8, 3, 0, nrhs=5)
+    part = block_partition(96, 96, 32, 32)
+    A = O.schwarz.as_csr(m, n, rp, c, v)
+    M = O.build_two_level(A, part, 9, tau=0.0, nev_max=16)
+    return dict(m=m, n=n, rp=rp, c=c, v=v, b=b, part=part, A=A, M=M)
+
+
+def test_multi_rhs_fixed_iterations(grid96):
+    d = grid96
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16, fixed_iters=6)
+    X, info = S.solve(d["b"], rtol=1e-8)
+    X = X.cpu().numpy()
+    assert X.shape == (5, d["n"])
+    for k in range(5):
+        xo, _ = O.pcg(d["A"], d["b"][k], d["M"].apply, fixed_iters=6)
+        assert rel(X[k], xo) < 1e-10, k
+    its, _ = S.batch_stats(5)
+    assert (its == 6).all()
+    S.close()
+
+
+@pytest.mark.parametrize("nrhs", [2, 5])
+def test_multi_rhs_matches_single_vector_path(grid96, nrhs):
+    d = grid96
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16)
+    X, info = S.solve(d["b"][:nrhs], rtol=1e-12)
+    its, relres = S.batch_stats(nrhs)
+    assert (relres <= 1e-12).all()
+    for k in range(nrhs):
+        x1, i1 = S.solve(d["b"][k], rtol=1e-12)
+        assert rel(X[k].cpu().numpy(), x1.cpu().numpy()) < 1e-10
+        assert abs(int(its[0, k]) - i1["iters"]) <= 1
+    S.close()
+
+
+@pytest.fixture(scope="module")
+def batch():
+    B = config_batch(nprob=4, nrhs=3, lo=1024, hi=4096, max_cols=700)
+    oracles = []
+    for q in range(B.nprob):
+        m, n, rp, c, v, part, N, b = B.problem(q)
+        A = O.schwarz.as_csr(m, n, rp, c, v)
+        oracles.append((A, O.build_two_level(A, part, N, tau=0.0, nev_max=8), b))
+    return B, oracles
+
+
+def _batched(B, **kw):
+    return L.Solver(B.m, B.n, B.row_ptr, B.col, B.val, B.part, B.nparts, problems=(B.m_off, B.n_off),
+                    nev_max=8, **kw)
+
+
+def test_batched_coarse_dimensions(batch):
+    B, oracles = batch
+    S = _batched(B)
+    ks = S.sizes()[:, 3]
+    off = 0
+    for q, (A, M, b) in enumerate(oracles):
+        N = len(M.ks)
+        assert ks[off:off + N].tolist() == list(M.ks), q
+        off += N
+    assert S.info()["n0"] == sum(M.n0 for _, M, _ in oracles)
+    S.close()
+
+
+def test_batched_fixed_iterations(batch):
+    B, oracles = batch
+    S = _batched(B, fixed_iters=6)
+    X, _ = S.solve(B.b, rtol=1e-8)
+    X = X.cpu().numpy()
+    for q, (A, M, b) in enumerate(oracles):
+        c0, c1 = int(B.n_off[q]), int(B.n_off[q + 1])
+        for k in range(b.shape[0]):
+            xo, _ = O.pcg(A, b[k], M.apply, fixed_iters=6)
+            assert rel(X[k, c0:c1], xo) < 1e-10, (q, k)
+    S.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_batched_converged(batch, prec):
+    B, oracles = batch
+    S = _batched(B, factor_prec=prec)
+    X, info = S.solve(B.b, rtol=1e-8)
+    its, relres = S.batch_stats(B.b.shape[0])
+    assert (relres <= 1e-8).all(), relres
+    X = X.cpu().numpy()
+    for q, (A, M, b) in enumerate(oracles):
+        c0, c1 = int(B.n_off[q]), int(B.n_off[q + 1])
+        for k in range(b.shape[0]):
+            xo, io = O.pcg(A, b[k], M.apply, rtol=1e-8)
+            # the per-pair test is the problem's own ||A_q^T b_q||
+            g = A.T @ b[k]
+            r = A.T @ (b[k] - A @ X[k, c0:c1])
+            assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(g), (q, k)
+            if prec == "f64":
+                assert abs(int(its[q, k]) - io["iters"]) <= 1, (q, k)
+    S.close()
+
+
+def test_batched_full_lanes(batch):
+    """32 right-hand sides (every lane of a warp busy) on the batched problems."""
+    B, oracles = batch
+    rng = np.random.default_rng(7)
+    b32 = rng.standard_normal((32, B.m))
+    S = _batched(B, factor_prec="f32")
+    X, info = S.solve(b32, rtol=1e-8)
+    its, relres = S.batch_stats(32)
+    assert (relres <= 1e-8).all()
+    X = X.cpu().numpy()
+    for q, (A, M, _) in enumerate(oracles):
+        r0, r1 = int(B.m_off[q]), int(B.m_off[q + 1])
+        c0, c1 = int(B.n_off[q]), int(B.n_off[q + 1])
+        for k in (0, 13, 31):
+            bk = b32[k, r0:r1]
+            r = A.T @ (bk - A @ X[k, c0:c1])
+            assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(A.T @ bk), (q, k)
+    S.close()
+
+
+def test_batched_rejects_crossing_rows(batch):
+    B, _ = batch
+    col = B.col.copy()
+    # move one entry of problem 1's first row into problem 0's columns
+    e = int(B.row_ptr[B.m_off[1]])
+    col[e] = 0
+    with pytest.raises(L.LSError) as ex:
+        L.Solver(B.m, B.n, B.row_ptr, col, B.val, B.part, B.nparts, problems=(B.m_off, B.n_off))
+    assert ex.value.status == L.LS_ERR_INVALID
+
+
+def test_too_many_rhs(grid96):
+    d = grid96
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16)
+    with pytest.raises(L.LSError) as ex:
+        S.solve(np.ones((33, d["m"])), rtol=1e-8)
+    assert ex.value.status == L.LS_ERR_UNSUPPORTED
+    S.close()

@@ -46,3 +46,21 @@ def test_batch_sizes():
     sides = config_batch_sizes()
     assert len(sides) == 64
     assert min(s * s for s in sides) >= 16000 and max(s * s for s in sides) <= 263000
+
+
+def test_batched_block_diagonal():
+    from workloads import config_batch
+    B = config_batch(nprob=5, nrhs=2, lo=1024, hi=4096, max_cols=600)
+    assert B.b.shape == (2, B.m) and B.m_off[-1] == B.m and B.n_off[-1] == B.n
+    assert B.row_ptr[0] == 0 and B.row_ptr[-1] == len(B.col) == len(B.val)
+    nid = 0
+    for q in range(B.nprob):
+        r0, r1 = B.m_off[q], B.m_off[q + 1]
+        cols = B.col[B.row_ptr[r0]:B.row_ptr[r1]]
+        assert cols.min() >= B.n_off[q] and cols.max() < B.n_off[q + 1]
+        ids = np.unique(B.part[B.n_off[q]:B.n_off[q + 1]])
+        assert ids[0] == nid and np.array_equal(ids, np.arange(ids[0], ids[-1] + 1))
+        nid = ids[-1] + 1
+        m, n, rp, c, v, part, N, b = B.problem(q)
+        assert m == 5 * n and rp[0] == 0 and c.max() < n and part.max() == N - 1 and b.shape == (2, m)
+    assert nid == B.nparts

@@ -16,6 +16,8 @@ from .grid import (  # noqa: F401
     config_precision,
     config_diff,
     config_batch_sizes,
+    config_batch,
+    BatchLS,
     paper_example,
     csr_from_dense,
 )

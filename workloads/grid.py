@@ -200,6 +200,72 @@ def config_batch_sizes(nprob: int = 64, lo: int = 16384, hi: int = 262144, seed:
     return [int(round(math.sqrt(x))) for x in ns]
 
 
+@dataclasses.dataclass
+class BatchLS:
+    """Independent problems stored as one block-diagonal CSR matrix: problem q owns the
+    rows [m_off[q], m_off[q+1]) and the columns [n_off[q], n_off[q+1]); its subdomain
+    ids follow those of problem q - 1.  b has shape [nrhs, m]."""
+    m: int
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    part: np.ndarray
+    nparts: int
+    b: np.ndarray
+    m_off: np.ndarray
+    n_off: np.ndarray
+    sides: list
+    name: str
+
+    @property
+    def nprob(self) -> int:
+        return len(self.sides)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def problem(self, q: int):
+        """(m, n, row_ptr, col, val, part, nparts, b) of problem q alone (local indices)."""
+        r0, r1 = int(self.m_off[q]), int(self.m_off[q + 1])
+        c0, c1 = int(self.n_off[q]), int(self.n_off[q + 1])
+        e0, e1 = int(self.row_ptr[r0]), int(self.row_ptr[r1])
+        part = self.part[c0:c1]
+        p0 = int(part.min())
+        return (r1 - r0, c1 - c0, self.row_ptr[r0:r1 + 1] - e0, self.col[e0:e1] - c0, self.val[e0:e1],
+                (part - p0).astype(np.int32), int(part.max()) - p0 + 1, self.b[:, r0:r1])
+
+
+def config_batch(nprob: int = 64, nrhs: int = 32, lo: int = 16384, hi: int = 262144, max_cols: int = 8192,
+                 size_seed: int = 999, name: str | None = None) -> BatchLS:
+    """Batched workload: nprob square grids with n log-uniform in [lo, hi] (sizes from
+    size_seed), each 4n random rows of 6 nonzeros within radius 2 (seed 1000 + q) plus
+    1e-2 I rows, nrhs right-hand sides b ~ N(0, 1), and uneven subdomains from seeded
+    recursive bisection (seed 2000 + q) into pieces of at most max_cols columns."""
+    sides = config_batch_sizes(nprob, lo, hi, size_seed)
+    rps, cols, vals, parts, bs = [], [], [], [], []
+    m_off, n_off = [0], [0]
+    nparts = 0
+    for q, s in enumerate(sides):
+        m, n, rp, c, v, b, _ = make_grid_ls(s, s, 4, 6, 2, 1000 + q, nrhs=nrhs)
+        part = bisection_partition(s, s, max_cols, 2000 + q)
+        nnz_before = (rps[-1][-1] if rps else 0)
+        rps.append((rp[1:] if rps else rp) + nnz_before)
+        cols.append(c + n_off[-1])
+        vals.append(v)
+        parts.append(part + nparts)
+        nparts += int(part.max()) + 1
+        bs.append(b.reshape(nrhs, m))
+        m_off.append(m_off[-1] + m)
+        n_off.append(n_off[-1] + n)
+    row_ptr = np.concatenate(rps).astype(np.int64)
+    return BatchLS(m=m_off[-1], n=n_off[-1], row_ptr=row_ptr, col=np.concatenate(cols).astype(np.int32),
+                   val=np.concatenate(vals), part=np.concatenate(parts).astype(np.int32), nparts=nparts,
+                   b=np.concatenate(bs, axis=1), m_off=np.array(m_off, np.int64), n_off=np.array(n_off, np.int64),
+                   sides=sides, name=name or f"batch{nprob}x{nrhs}-n[{lo},{hi}]-r2k6-sub{max_cols}")
+
+
 def paper_example():
     """The 5x4 worked example of Section 3 with Omega_I1 = {1, 3}, Omega_I2 = {2, 4} (1-based)."""
     A = np.array([[1, 0, 6, 0],
