@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-side", type=int, default=256, help="grid side of the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision", "batch"],
                     help="solve: the timed benchmark line; nsweep: iterations/setup vs subdomain count "
-                         "(blocks 128/64/32); precision: errors of every form on the column-scaled workload")
+                         "(blocks 128/64/32); precision: errors of every form on the column-scaled workload; "
+                         "batch: 64 independent problems x 32 right-hand sides in shared launches")
+    ap.add_argument("--nprob", type=int, default=64)
+    ap.add_argument("--nrhs", type=int, default=32)
     return ap.parse_args()
 
 
@@ -433,6 +436,86 @@ def run_precision(args):
                       "rows": rows}), flush=True)
 
 
+def run_batch(args):
+    """Batched workload: 64 independent problems (n log-uniform in [16384, 262144],
+    square grids, 4n rows of 6 nonzeros within radius 2 plus 1e-2 I, uneven bisection
+    subdomains of at most 8192 columns), 32 right-hand sides each, FP32 local factors
+    inside FP64 flexible CG, one CUDA graph per iteration.  A step is one ls_solve of
+    all problems and right-hand sides from x = 0 to every pair's own 1e-8 test."""
+    torch, dev = _device_setup()
+    import numpy as np
+    from paper_2107_09006_gb300 import Solver, ls_solve
+    from workloads import config_batch
+    t = time.time()
+    B = config_batch(nprob=args.nprob, nrhs=args.nrhs)
+    log(f"[batch] generated in {time.time() - t:.1f}s: m={B.m} n={B.n} nnz={B.nnz} N={B.nparts}")
+    stream = torch.cuda.current_stream(dev)
+    t = time.time()
+    S = Solver(B.m, B.n, B.row_ptr, B.col, B.val, B.part, B.nparts, device=dev, stream=stream,
+               problems=(B.m_off, B.n_off), nev_max=args.nev, factor_prec=args.prec, time_kernels=1, maxit=500)
+    torch.cuda.synchronize(dev)
+    setup = time.time() - t
+    si, st = S.info(), S.storage()
+    log(f"[batch] setup {setup:.1f}s (eig+coarse {si['t_eig']:.1f}s) n0={si['n0']} fac={st['fac_elems']}")
+    R = args.nrhs
+    b_dev = torch.as_tensor(B.b, device=dev)
+    x_dev = torch.empty((R, B.n), dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        ls_solve(S.h, b_dev, R, args.rtol, x_dev)
+    ck = Clocks(dev.index or 0)
+    ck.start()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [ls_solve(S.h, b_dev, R, args.rtol, x_dev) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = ck.stop()
+    sec = e0.elapsed_time(e1) / 1000.0 / args.steps
+    its, relres = S.batch_stats(R)
+    inf = infos[-1]
+    nl = max(inf["local_launches"], 1)
+    ms_local = inf["ms_local"] / nl
+    es = {"f64": 8, "f32": 4, "bf16": 2}[args.prec]
+    ta = 8 if args.prec == "f64" else 4
+    fac_bytes = 2 * st["fac_elems"] * es
+    local_bytes = fac_bytes + st["total_local"] * R * 16 + st["total_local"] * 12 + \
+        2 * st["total_blocks"] * 1024 * ta  # factor twice, R gather + R write, maps, spill
+    local_flops = 4.0 * st["fac_elems"] * R  # 2 flops per element per sweep per right-hand side
+    # end to end from pinned host b to pinned host x
+    bh = torch.as_tensor(B.b).pin_memory()
+    xh = torch.empty((R, B.n), dtype=torch.float64).pin_memory()
+    ls_solve(S.h, bh, R, args.rtol, xh)
+    torch.cuda.synchronize(dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        ls_solve(S.h, bh, R, args.rtol, xh)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e = f0.elapsed_time(f1) / 1000.0 / args.steps
+    pairs = B.nprob * R
+    out = {
+        "report": "batch", "metric": "batched LS solves/s to 1e-8 (problem x rhs pairs)",
+        "value": pairs / sec, "unit": "solves/s", "s_per_step": sec, "pairs": pairs,
+        "e2e": {"value": pairs / e2e, "unit": "solves/s", "h2d_bytes_per_step": int(B.m) * R * 8,
+                "d2h_bytes_per_step": int(B.n) * R * 8},
+        "workload": {"name": B.name, "nprob": B.nprob, "nrhs": R, "m": int(B.m), "n": int(B.n), "nnz": B.nnz,
+                     "subdomains": B.nparts, "nev_max": args.nev, "form": args.prec, "rtol": args.rtol},
+        "iterations": {"max": int(its.max()), "min": int(its.min()), "mean": float(its.mean())},
+        "relres_true_max": float(relres.max()), "setup_s": setup, "eig_coarse_s": si["t_eig"], "n0": si["n0"],
+        "ms_per_iteration_kernels": inf["ms_iter"] / max(inf["iters"], 1),
+        "local_solve": {"ms_per_launch": ms_local, "bytes_per_launch": local_bytes,
+                        "GBps": local_bytes / (ms_local * 1e-3) / 1e9,
+                        "TFLOPs": local_flops / (ms_local * 1e-3) / 1e12},
+        "spmm_pair_ms_per_iter": inf["ms_spmv"] / max(inf["iters"], 1),
+        "coarse_ms_per_iter": inf["ms_coarse"] / max(inf["iters"], 1),
+        "launches_per_step": inf["launches"], "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    S.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -441,5 +524,7 @@ if __name__ == "__main__":
         run_nsweep(a)
     elif a.mode == "precision":
         run_precision(a)
+    elif a.mode == "batch":
+        run_batch(a)
     else:
         run_ours(a)
