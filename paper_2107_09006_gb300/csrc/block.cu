@@ -55,6 +55,7 @@ void ensure_buffers(ls_handle* h, int R) {
   B.Y.alloc((size_t)h->total_local * R);
   B.R0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   B.Y0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
+  if (B.ZT.p) B.Y0f.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   B.R = R;
 }
 
@@ -75,10 +76,15 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   lsq::launch_b_local(h->prec, a, B.local_grid, st);
   if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
   const bool coarse = h->coarse && h->n0 > 0;
+  const bool zt = coarse && B.ZT.p != nullptr;
   if (coarse) {
-    lsq::launch_b_restrict(h->N, R, h->int_off.p, h->int_glob.p, h->zoff.p, h->coff.p, h->Z.p, Rin, B.R0.p, st);
+    if (zt)
+      lsq::launch_b_restrict32(h->N, R, h->int_off.p, h->int_glob.p, h->coff.p, B.zt_off.p, B.ZT.p, Rin, B.R0.p, st);
+    else
+      lsq::launch_b_restrict(h->N, R, h->int_off.p, h->int_glob.p, h->zoff.p, h->coff.p, h->Z.p, Rin, B.R0.p, st);
     const lsq::CoarseBlocks cb{h->cb_prob_of_sub.p, h->cb_base.p, h->cb_ld.p, h->cb_c0.p};
-    lsq::launch_b_coarse(B.nct, R, B.ct_prob.p, B.ct_row.p, cb, B.n0q.p, h->Xinv.p, B.R0.p, B.Y0.p, st);
+    lsq::launch_b_coarse(B.nct, R, B.ct_prob.p, B.ct_row.p, cb, B.n0q.p, h->Xinv.p, B.R0.p, B.Y0.p,
+                         zt ? B.Y0f.p : nullptr, st);
   }
   if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
   lsq::BScatterArgs s{};
@@ -88,6 +94,7 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.Y = B.Y.p;
   s.coarse = coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p; s.coff = h->coff.p;
   s.nI = h->nI.p; s.Z = h->Z.p; s.Y0 = B.Y0.p;
+  if (zt) { s.ZT = B.ZT.p; s.zt_off = B.zt_off.p; s.Y0f = B.Y0f.p; }
   s.Rv = Rin; s.Rold = flex ? B.Rold.p : nullptr; s.Zout = Zout;
   s.part1 = B.parts.p; s.part2 = B.parts.p + (size_t)B.nchunks * 32;
   lsq::launch_b_scatter(chunks(h), s, st);
@@ -202,6 +209,15 @@ void block_plan(ls_handle* h) {
     }
   }
   B.nct = (int)cp.size();
+  // mixed forms: the coarse restriction and prolongation run in FP32 from a transposed
+  // copy of the basis (the coarse solve itself stays FP64)
+  if (h->prec != LS_PREC_F64 && h->coarse && h->n0 > 0) {
+    std::vector<int64_t> zo(h->N + 1, 0);
+    for (int i = 0; i < h->N; ++i) zo[i + 1] = zo[i] + (int64_t)h->h_nI[i] * ((h->h_k[i] + 3) & ~3);
+    B.zt_off.upload(zo, st);
+    B.ZT.alloc(std::max<int64_t>(zo[h->N], 1));
+    lsq::launch_b_ztrans(h->N, h->int_off.p, h->zoff.p, h->coff.p, B.zt_off.p, h->Z.p, B.ZT.p, st);
+  }
   B.ct_prob.upload(cp, st);
   B.ct_row.upload(cr, st);
   B.n0q.upload(n0q, st);

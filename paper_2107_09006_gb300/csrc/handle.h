@@ -97,6 +97,9 @@ struct BlockState {
   bool local_ok = false;  // the ring fits the shared memory of one CTA
   // coarse solve tiles: (problem, 32-row tile) pairs
   DevBuf<int32_t> ct_prob, ct_row, n0q;
+  // mixed forms: FP32 transposed coarse basis and FP32 copy of the coarse solution
+  DevBuf<float> ZT, Y0f;
+  DevBuf<int64_t> zt_off;
   int nct = 0;
   std::vector<int> h_its;
   std::vector<double> h_rel;

@@ -260,7 +260,22 @@ __global__ void __launch_bounds__(kThreads) k_b_scatter(BChunks ch, BScatterArgs
       for (int64_t j = s + w * L.G + L.g; j < e; j += kWarps * L.G) {
         double z = 0.0;
         for (int64_t t = a.map_ptr[j]; t < a.map_ptr[j + 1]; ++t) z += a.Y[a.map_idx[t] * R + L.k];
-        if (a.coarse) {
+        if (a.coarse && a.ZT) {
+          const int i = a.part[j];
+          const int cc = a.coff[i], kk = a.coff[i + 1] - cc, kp = (kk + 3) & ~3;
+          const float4* z4 = reinterpret_cast<const float4*>(a.ZT + a.zt_off[i] + (int64_t)a.jj_of[j] * kp);
+          const float* y0 = a.Y0f + (int64_t)cc * R + L.k;
+          float zc = 0.f;
+          for (int t4 = 0; 4 * t4 < kk; ++t4) {
+            const float4 zz = z4[t4];
+            const int t = 4 * t4;
+            zc += zz.x * y0[(int64_t)t * R];
+            if (t + 1 < kk) zc += zz.y * y0[(int64_t)(t + 1) * R];
+            if (t + 2 < kk) zc += zz.z * y0[(int64_t)(t + 2) * R];
+            if (t + 3 < kk) zc += zz.w * y0[(int64_t)(t + 3) * R];
+          }
+          z += (double)zc;
+        } else if (a.coarse) {
           const int i = a.part[j];
           const int cc = a.coff[i], kk = a.coff[i + 1] - cc;
           const int64_t nIi = a.nI[i];
@@ -311,11 +326,76 @@ __global__ void __launch_bounds__(kThreads) k_b_restrict(int R, int Rp, const in
   }
 }
 
+// FP32 transposed copy of the coarse basis: ZT[zt_off[i] + jj * kp + t] = Zbar_i[t, jj]
+// (kp = k_i rounded up to 4, so one interior column's k_i values are 16-byte aligned).
+__global__ void __launch_bounds__(kThreads) k_b_ztrans(const int64_t* __restrict__ int_off,
+                                                       const int64_t* __restrict__ zoff,
+                                                       const int32_t* __restrict__ coff,
+                                                       const int64_t* __restrict__ zt_off,
+                                                       const double* __restrict__ Z, float* __restrict__ ZT) {
+  const int i = blockIdx.x;
+  const int kk = coff[i + 1] - coff[i], kp = (kk + 3) & ~3;
+  const int64_t nIi = int_off[i + 1] - int_off[i];
+  for (int64_t e = threadIdx.x; e < nIi * kp; e += blockDim.x) {
+    const int64_t jj = e / kp;
+    const int t = (int)(e % kp);
+    ZT[zt_off[i] + e] = t < kk ? (float)Z[zoff[i] + (int64_t)t * nIi + jj] : 0.f;
+  }
+}
+
+// FP32 restriction R0[(c0 + t), k] = sum_jj ZT[jj, t] R[Omega_I,i[jj], k] for the mixed
+// forms: warps split the interior columns, lane k keeps 32 coarse sums in registers,
+// the warps' sums meet in shared memory.
+__global__ void __launch_bounds__(kThreads) k_b_restrict32(int R, const int64_t* __restrict__ int_off,
+                                                           const int32_t* __restrict__ int_glob,
+                                                           const int32_t* __restrict__ coff,
+                                                           const int64_t* __restrict__ zt_off,
+                                                           const float* __restrict__ ZT,
+                                                           const double* __restrict__ Rv, double* __restrict__ R0) {
+  __shared__ float red[kWarps][32][33];
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cc = coff[i], kk = coff[i + 1] - cc, kp = (kk + 3) & ~3;
+  const int64_t io = int_off[i];
+  const int nIi = (int)(int_off[i + 1] - io);
+  const float* Zi = ZT + zt_off[i];
+  for (int tb = 0; tb < kk; tb += 32) {
+    const int tn = min(32, kk - tb);
+    float acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.f;
+    for (int jj = w; jj < nIi; jj += kWarps) {
+      const float rv = lane < R ? (float)Rv[(int64_t)int_glob[io + jj] * R + lane] : 0.f;
+      const float4* z4 = reinterpret_cast<const float4*>(Zi + (int64_t)jj * kp + tb);
+#pragma unroll
+      for (int t4 = 0; t4 < 8; ++t4) {
+        if (4 * t4 < tn) {
+          const float4 z = z4[t4];
+          acc[4 * t4 + 0] += z.x * rv; acc[4 * t4 + 1] += z.y * rv;
+          acc[4 * t4 + 2] += z.z * rv; acc[4 * t4 + 3] += z.w * rv;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) red[w][t][lane] = acc[t];
+    __syncthreads();
+    for (int e = threadIdx.x; e < tn * 32; e += blockDim.x) {
+      const int t = e >> 5, k = e & 31;
+      float s = 0.f;
+#pragma unroll
+      for (int u = 0; u < kWarps; ++u) s += red[u][t][k];
+      if (k < R) R0[(int64_t)(cc + tb + t) * R + k] = (double)s;
+    }
+    __syncthreads();
+  }
+}
+
 // Y0 = C00_q^{-1} R0 on every problem's dense block; one block per (problem, 32-row tile).
 __global__ void __launch_bounds__(kThreads) k_b_coarse(int R, const int32_t* __restrict__ ct_prob,
                                                        const int32_t* __restrict__ ct_row, CoarseBlocks cb,
                                                        const int32_t* __restrict__ n0q, const double* __restrict__ Xinv,
-                                                       const double* __restrict__ R0, double* __restrict__ Y0) {
+                                                       const double* __restrict__ R0, double* __restrict__ Y0,
+                                                       float* __restrict__ Y0f) {
   const int q = ct_prob[blockIdx.x], rt = ct_row[blockIdx.x];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane >= R) return;
@@ -331,7 +411,10 @@ __global__ void __launch_bounds__(kThreads) k_b_coarse(int R, const int32_t* __r
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    if (rbase + u < nq) Y0[(int64_t)(c0 + rbase + u) * R + lane] = acc[u];
+    if (rbase + u < nq) {
+      Y0[(int64_t)(c0 + rbase + u) * R + lane] = acc[u];
+      if (Y0f) Y0f[(int64_t)(c0 + rbase + u) * R + lane] = (float)acc[u];
+    }
 }
 
 // ---- layout conversions ---------------------------------------------------------------
@@ -680,9 +763,20 @@ void launch_b_restrict(int N, int R, const int64_t* int_off, const int32_t* int_
 }
 
 void launch_b_coarse(int ntiles, int R, const int32_t* ct_prob, const int32_t* ct_row, const CoarseBlocks& cb,
-                     const int32_t* n0q, const double* Xinv, const double* R0, double* Y0, cudaStream_t st) {
+                     const int32_t* n0q, const double* Xinv, const double* R0, double* Y0, float* Y0f,
+                     cudaStream_t st) {
   if (ntiles <= 0) return;
-  k_b_coarse<<<ntiles, kThreads, 0, st>>>(R, ct_prob, ct_row, cb, n0q, Xinv, R0, Y0);
+  k_b_coarse<<<ntiles, kThreads, 0, st>>>(R, ct_prob, ct_row, cb, n0q, Xinv, R0, Y0, Y0f);
+}
+
+void launch_b_ztrans(int N, const int64_t* int_off, const int64_t* zoff, const int32_t* coff, const int64_t* zt_off,
+                     const double* Z, float* ZT, cudaStream_t st) {
+  k_b_ztrans<<<N, kThreads, 0, st>>>(int_off, zoff, coff, zt_off, Z, ZT);
+}
+
+void launch_b_restrict32(int N, int R, const int64_t* int_off, const int32_t* int_glob, const int32_t* coff,
+                         const int64_t* zt_off, const float* ZT, const double* Rv, double* R0, cudaStream_t st) {
+  k_b_restrict32<<<N, kThreads, 0, st>>>(R, int_off, int_glob, coff, zt_off, ZT, Rv, R0);
 }
 
 void launch_b_load_rows(int64_t m, int R, const int32_t* perm, const double* Bu, double* Bb, cudaStream_t st) {

@@ -172,6 +172,7 @@ struct BScatterArgs {
   const int64_t* map_ptr; const int64_t* map_idx; const double* Y;  // local solutions [sum n_i][R]
   int coarse; const int32_t* part; const int32_t* jj_of; const int64_t* zoff; const int32_t* coff;
   const int32_t* nI; const double* Z; const double* Y0;
+  const float* ZT; const int64_t* zt_off; const float* Y0f;  // FP32 prolongation when ZT != nullptr
   const double* Rv; const double* Rold; double* Zout; double* part1; double* part2;
 };
 constexpr int kBlockRingBytes = 32768;  // shared-memory ring of factor tiles per CTA
@@ -201,7 +202,14 @@ void launch_b_scatter(const BChunks& ch, const BScatterArgs& a, cudaStream_t st)
 void launch_b_restrict(int N, int R, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff,
                        const int32_t* coff, const double* Z, const double* Rv, double* R0, cudaStream_t st);
 void launch_b_coarse(int ntiles, int R, const int32_t* ct_prob, const int32_t* ct_row, const CoarseBlocks& cb,
-                     const int32_t* n0q, const double* Xinv, const double* R0, double* Y0, cudaStream_t st);
+                     const int32_t* n0q, const double* Xinv, const double* R0, double* Y0, float* Y0f,
+                     cudaStream_t st);
+// FP32 transposed coarse basis (mixed forms): ZT[zt_off[i] + jj * kp_i + t] = Zbar_i[t, jj],
+// kp_i = k_i rounded up to 4; restriction with it.
+void launch_b_ztrans(int N, const int64_t* int_off, const int64_t* zoff, const int32_t* coff, const int64_t* zt_off,
+                     const double* Z, float* ZT, cudaStream_t st);
+void launch_b_restrict32(int N, int R, const int64_t* int_off, const int32_t* int_glob, const int32_t* coff,
+                         const int64_t* zt_off, const float* ZT, const double* Rv, double* R0, cudaStream_t st);
 void launch_b_load_rows(int64_t m, int R, const int32_t* perm, const double* Bu, double* Bb, cudaStream_t st);
 void launch_b_store_cols(int64_t n, int R, const double* Xb, double* Xu, cudaStream_t st);
 // b = a - b over len entries
