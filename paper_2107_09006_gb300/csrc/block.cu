@@ -56,6 +56,11 @@ void ensure_buffers(ls_handle* h, int R) {
   B.R0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   B.Y0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   if (B.ZT.p) B.Y0f.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
+  if (B.use_tc && !B.Lsw.p) {
+    B.Lsw.alloc(h->fac_elems);
+    lsq::launch_b_swizzle(h->fac_elems, h->L32.p, B.Lsw.p, h->st);
+    check_launch("swizzled factor copy");
+  }
   B.R = R;
 }
 
@@ -73,7 +78,13 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
   a.Rv = Rin; a.Y = B.Y.p; a.R = R; a.Vg = B.Vg.p; a.ring = B.ring;
   a.err = h->scal.p + lsq::S_ERR;
-  lsq::launch_b_local(h->prec, a, B.local_grid, st);
+  if (B.use_tc) {
+    a.fac = B.Lsw.p;
+    a.tsc = nullptr;
+    lsq::launch_b_local_tc(a, B.local_grid, st);
+  } else {
+    lsq::launch_b_local(h->prec, a, B.local_grid, st);
+  }
   if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
   const bool coarse = h->coarse && h->n0 > 0;
   const bool zt = coarse && B.ZT.p != nullptr;
@@ -194,8 +205,9 @@ void block_plan(ls_handle* h) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
   const size_t need = lsq::block_local_smem(fac_bytes(h->prec), arith_bytes(h->prec), B.ring);
   B.local_ok = need <= (size_t)optin;
+  B.use_tc = h->prec == LS_PREC_F32;
   if (B.local_ok) {
-    const int occ = lsq::block_local_occupancy(h->prec, B.ring);
+    const int occ = B.use_tc ? lsq::block_local_tc_occupancy(B.ring) : lsq::block_local_occupancy(h->prec, B.ring);
     B.local_grid = std::max(1, std::min(h->N, sms * std::max(occ, 1)));
     B.Vg.alloc((size_t)h->total_blocks * 1024 * arith_bytes(h->prec));
   }

@@ -95,6 +95,8 @@ struct BlockState {
   int local_grid = 0;
   int ring = 0;           // solution tiles kept in shared memory (widest block row)
   bool local_ok = false;  // the ring fits the shared memory of one CTA
+  bool use_tc = false;    // FP32 factors: tensor-core local solves from the swizzled copy
+  DevBuf<float> Lsw;      // TF32-rounded swizzled factor tiles (made at the first block solve)
   // coarse solve tiles: (problem, 32-row tile) pairs
   DevBuf<int32_t> ct_prob, ct_row, n0q;
   // mixed forms: FP32 transposed coarse basis and FP32 copy of the coarse solution

@@ -665,6 +665,224 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
   }
 }
 
+// ---- tensor-core local solves (FP32 factors) ------------------------------------------
+// Each 32 x 32 block step is a product of a factor tile (or its transpose) with the
+// 32 x R solution tile, done as 2 x 4 warp tiles of m16n8k8 TF32 MMAs: warp w owns the
+// output rows [16 (w / 4), +16) and right-hand sides [8 (w % 4), +8).  The solution
+// operand is split into a TF32 head and a TF32 tail (two MMAs), which keeps it at
+// about FP32 accuracy; the factor is TF32 (stored pre-rounded).  Factor and solution
+// tiles are row-major with the swizzle (r, c) -> 32 r + ((c + 8 (r % 4) + 4 ((r / 4) % 2)) % 32):
+// the fragments of T, of T^T and of the solution tile then all hit 32 distinct banks.
+
+__device__ __forceinline__ int swz(int r, int c) { return r * kT + ((c + 8 * (r & 3) + 4 * ((r >> 2) & 1)) & 31); }
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// c += op(T) V on the warp's 16 x 8 output block; op(T) = T or T^T.
+template <bool TRANS>
+__device__ __forceinline__ void tile_mma(const float* T, const float* V, float c[4], int mb, int nb, int g, int t) {
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const int r0 = mb * 16 + g, k0 = ks * 8 + t;
+    uint32_t a[4];
+    if (!TRANS) {
+      a[0] = __float_as_uint(T[swz(r0, k0)]);     a[1] = __float_as_uint(T[swz(r0 + 8, k0)]);
+      a[2] = __float_as_uint(T[swz(r0, k0 + 4)]); a[3] = __float_as_uint(T[swz(r0 + 8, k0 + 4)]);
+    } else {
+      a[0] = __float_as_uint(T[swz(k0, r0)]);     a[1] = __float_as_uint(T[swz(k0, r0 + 8)]);
+      a[2] = __float_as_uint(T[swz(k0 + 4, r0)]); a[3] = __float_as_uint(T[swz(k0 + 4, r0 + 8)]);
+    }
+    const float v0 = V[swz(k0, nb * 8 + g)], v1 = V[swz(k0 + 4, nb * 8 + g)];
+    const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
+    const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
+    mma_tf32(c, a, h0, h1);
+    mma_tf32(c, a, l0, l1);
+  }
+}
+
+// The warp's accumulator elements: (row, col) of c[2 h + j] = (16 mb + g + 8 h, 8 nb + 2 t + j).
+__device__ __forceinline__ float2* frag_ptr(float* tile, int mb, int nb, int g, int t, int h) {
+  return reinterpret_cast<float2*>(tile + swz(mb * 16 + g + 8 * h, nb * 8 + 2 * t));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int S = kBlockRingBytes / (kT * kT * 4);
+  float* fring = reinterpret_cast<float*>(smem);
+  float* vring = reinterpret_cast<float*>(smem + kBlockRingBytes);
+  float* tin = vring + (size_t)a.ring * kT * kT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tin + kT * kT);
+  int* sh = reinterpret_cast<int*>(bars + S);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int mb = w >> 2, nb = w & 3, g = lane >> 2, t4 = lane & 3;
+  const int R = a.R, RING = a.ring;
+  const float* fac = reinterpret_cast<const float*>(a.fac);
+  float* spill = reinterpret_cast<float*>(a.Vg);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) bar_init(&bars[s], 1);
+    sh[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t q = 0, issued = 0;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned tk = atomicAdd(a.qctr, 1u);
+      sh[0] = tk < (unsigned)a.N ? a.order[tk] : -1;
+    }
+    __syncthreads();
+    const int i = sh[0];
+    if (i < 0) break;
+    const int64_t o0 = a.om_off[i];
+    const int ni = (int)(a.om_off[i + 1] - o0);
+    const int64_t b0 = a.blk_off[i];
+    const int nbk = (int)(a.blk_off[i + 1] - b0);
+    const int32_t* tf = a.blk_tf + b0;
+    const int64_t T0 = a.blk_poff[b0] / (kT * kT);
+    const int64_t ntile = a.blk_poff[b0 + nbk] / (kT * kT) - T0;
+    int64_t pnext = 0;
+    auto issue = [&]() {
+      const int64_t tile = pnext < ntile ? T0 + pnext : T0 + 2 * ntile - 1 - pnext;
+      const int stage = (int)(issued % S);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_expect_tx(&bars[stage], kT * kT * 4);
+      copy_g2s(fring + (size_t)stage * kT * kT, fac + tile * kT * kT, kT * kT * 4, &bars[stage]);
+      ++pnext;
+      ++issued;
+    };
+    if (tid == 0)
+      while (pnext < 2 * ntile && issued < q + S) issue();
+    auto wait_tile = [&]() -> const float* {
+      const int stage = (int)(q % S);
+      const uint32_t parity = (q / S) & 1u;
+      if (!bar_try_wait(&bars[stage], parity)) {
+        const long long c0 = clock64();
+        bool ok = false;
+        while (!(ok = bar_try_wait(&bars[stage], parity)))
+          if (clock64() - c0 > kSpinCycles) break;
+        if (!ok) sh[1] = 1;
+      }
+      return fring + (size_t)stage * kT * kT;
+    };
+    auto release = [&]() -> bool {
+      __syncthreads();
+      ++q;
+      if (sh[1]) return false;
+      if (tid == 0 && pnext < 2 * ntile) issue();
+      return true;
+    };
+    bool ok = true;
+    // forward sweep
+    for (int b = 0; b < nbk && ok; ++b) {
+      for (int e = tid; e < kT * kT; e += kThreads) {
+        const int rr = e >> 5, k = e & 31, l = b * kT + rr;
+        float v = 0.f;
+        if (l < ni && k < R) v = (float)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]);
+        tin[swz(rr, k)] = v;
+      }
+      __syncthreads();
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int t = tf[b]; t < b && ok; ++t) {
+        const float* T = wait_tile();
+        tile_mma<false>(T, vring + (size_t)(t % RING) * kT * kT, c, mb, nb, g, t4);
+        ok = release();
+      }
+      if (!ok) break;
+      const float* D = wait_tile();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2* p = frag_ptr(tin, mb, nb, g, t4, h);
+        float2 v = *p;
+        v.x -= c[2 * h];
+        v.y -= c[2 * h + 1];
+        *p = v;
+      }
+      __syncthreads();
+      float y[4] = {0.f, 0.f, 0.f, 0.f};
+      tile_mma<false>(D, tin, y, mb, nb, g, t4);
+      float* vb = vring + (size_t)(b % RING) * kT * kT;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) *frag_ptr(vb, mb, nb, g, t4, h) = make_float2(y[2 * h], y[2 * h + 1]);
+      if (b < nbk - RING) {
+        float* sp = spill + (size_t)(b0 + b) * kT * kT;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) *frag_ptr(sp, mb, nb, g, t4, h) = make_float2(y[2 * h], y[2 * h + 1]);
+      }
+      ok = release();
+    }
+    // backward sweep
+    for (int b = nbk - 1; b >= 0 && ok; --b) {
+      const float* D = wait_tile();
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      tile_mma<true>(D, vring + (size_t)(b % RING) * kT * kT, x, mb, nb, g, t4);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        *frag_ptr(tin, mb, nb, g, t4, h) = make_float2(x[2 * h], x[2 * h + 1]);
+        const int l = b * kT + mb * 16 + g + 8 * h;
+        const int k = nb * 8 + 2 * t4;
+        if (l < ni) {
+          const double sc = a.eqs[o0 + l];
+          if (k < R) a.Y[(o0 + l) * R + k] = (double)x[2 * h] * sc;
+          if (k + 1 < R) a.Y[(o0 + l) * R + k + 1] = (double)x[2 * h + 1] * sc;
+        }
+      }
+      ok = release();
+      for (int t = b - 1; t >= tf[b] && ok; --t) {
+        const float* T = wait_tile();
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        tile_mma<true>(T, tin, s, mb, nb, g, t4);
+        float* vt = vring + (size_t)(t % RING) * kT * kT;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float2* p = frag_ptr(vt, mb, nb, g, t4, h);
+          float2 v = *p;
+          v.x -= s[2 * h];
+          v.y -= s[2 * h + 1];
+          *p = v;
+        }
+        ok = release();
+      }
+      if (ok && b - RING >= 0) {
+        const float4* sp = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT);
+        float4* vb = reinterpret_cast<float4*>(vring + (size_t)(b % RING) * kT * kT);
+        for (int e = tid; e < kT * kT / 4; e += kThreads) vb[e] = sp[e];
+        __syncthreads();
+      }
+    }
+    if (!ok) break;
+  }
+  if (sh[1]) {
+    if (tid == 0) {
+      a.err[0] = 1.0;
+      for (uint32_t qq = q; qq < issued; ++qq) {
+        const long long c0 = clock64();
+        while (!bar_try_wait(&bars[qq % S], (qq / S) & 1u))
+          if (clock64() - c0 > kSpinCycles) break;
+      }
+    }
+  }
+}
+
+// FP32 solve storage (column-major tiles) -> TF32-rounded swizzled row-major tiles.
+__global__ void k_b_swizzle(int64_t nelem, const float* __restrict__ src, float* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nelem; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = e >> 10;
+    const int r = (int)(e & 31), c = (int)((e >> 5) & 31);  // source element (c * 32 + r)
+    dst[(tile << 10) + swz(r, c)] = __uint_as_float(tf32_bits(src[e]));
+  }
+}
+
 int grid_rows(int64_t rows, int G) {
   const int64_t warps = (rows + G - 1) / G;
   const int64_t g = (warps + kWarps - 1) / kWarps;
@@ -725,6 +943,30 @@ void launch_b_local(int prec, const BLocalArgs& a, int grid, cudaStream_t st) {
   if (prec == 0) local_impl<double, double>(a, grid, st);
   else if (prec == 1) local_impl<float, float>(a, grid, st);
   else local_impl<__nv_bfloat16, float>(a, grid, st);
+}
+
+int block_local_tc_occupancy(int ring) {
+  const size_t sm = block_local_smem(4, 4, ring);
+  static size_t raised = 0;
+  if (sm > 48 * 1024 && sm > raised) {
+    cudaFuncSetAttribute(k_b_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raised = sm;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_local_tc, kThreads, sm) != cudaSuccess) occ = 0;
+  return occ;
+}
+
+void launch_b_local_tc(const BLocalArgs& a, int grid, cudaStream_t st) {
+  cudaMemsetAsync(a.qctr, 0, sizeof(unsigned), st);
+  k_b_local_tc<<<grid, kThreads, block_local_smem(4, 4, a.ring), st>>>(a);
+}
+
+void launch_b_swizzle(int64_t nelem, const float* src, float* dst, cudaStream_t st) {
+  int64_t g = (nelem + kThreads - 1) / kThreads;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  k_b_swizzle<<<(int)g, kThreads, 0, st>>>(nelem, src, dst);
 }
 
 void launch_b_spmm_csr(const CsrDev& A, const double* X, double* Y, int R, cudaStream_t st) {

@@ -189,6 +189,11 @@ struct BLocalArgs {
 size_t block_local_smem(int fac_bytes, int arith_bytes, int ring);
 int block_local_occupancy(int prec, int ring);
 void launch_b_local(int prec, const BLocalArgs& a, int grid, cudaStream_t st);
+// FP32 factors on the tensor cores (TF32 MMA): a.fac is the swizzled TF32 copy that
+// launch_b_swizzle makes from the FP32 solve storage.
+int block_local_tc_occupancy(int ring);
+void launch_b_local_tc(const BLocalArgs& a, int grid, cudaStream_t st);
+void launch_b_swizzle(int64_t nelem, const float* src, float* dst, cudaStream_t st);
 void launch_b_spmm_csr(const CsrDev& A, const double* X, double* Y, int R, cudaStream_t st);
 void launch_b_spmm_csc(const BChunks& ch, const CscDev& At, const double* Q, double* W, int R, const double* D,
                        double* part, cudaStream_t st);

@@ -165,3 +165,19 @@ def test_too_many_rhs(grid96):
         S.solve(np.ones((33, d["m"])), rtol=1e-8)
     assert ex.value.status == L.LS_ERR_UNSUPPORTED
     S.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_multi_rhs_mixed_forms_track_single_vector_path(grid96, prec):
+    """Mixed forms (FP32 factors on the tensor cores, BF16 factors on the CUDA cores):
+    every right-hand side meets 1e-10 within two iterations of the single-vector path."""
+    d = grid96
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16, factor_prec=prec)
+    X, info = S.solve(d["b"], rtol=1e-10)
+    its, relres = S.batch_stats(5)
+    assert (relres <= 1e-10).all()
+    for k in range(5):
+        x1, i1 = S.solve(d["b"][k], rtol=1e-10)
+        assert abs(int(its[0, k]) - i1["iters"]) <= 2, (k, its[0, k], i1["iters"])
+        assert rel(X[k].cpu().numpy(), x1.cpu().numpy()) < 1e-7
+    S.close()
