@@ -572,10 +572,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
       return fring + (size_t)stage * kT * kT;
     };
     // every thread is done with the current stage: hand it back to the producer
+    // (on a give-up q keeps pointing at the tile that was waited for, so the final
+    // drain covers it)
     auto release = [&]() -> bool {
       __syncthreads();
-      ++q;
       if (sh[1]) return false;
+      ++q;
       if (tid == 0 && pnext < 2 * ntile) issue();
       return true;
     };
@@ -689,9 +691,11 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// c += op(T) V on the warp's 16 x 8 output block; op(T) = T or T^T.
+// c += op(T) V on the warp's 16 x 8 output block; op(T) = T or T^T.  The head and
+// tail products go to two accumulators (two independent MMA chains), summed at the end.
 template <bool TRANS>
 __device__ __forceinline__ void tile_mma(const float* T, const float* V, float c[4], int mb, int nb, int g, int t) {
+  float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int ks = 0; ks < 4; ++ks) {
     const int r0 = mb * 16 + g, k0 = ks * 8 + t;
@@ -707,8 +711,10 @@ __device__ __forceinline__ void tile_mma(const float* T, const float* V, float c
     const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
     const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
     mma_tf32(c, a, h0, h1);
-    mma_tf32(c, a, l0, l1);
+    mma_tf32(d, a, l0, l1);
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) c[u] += d[u];
 }
 
 // The warp's accumulator elements: (row, col) of c[2 h + j] = (16 mb + g + 8 h, 8 nb + 2 t + j).
@@ -775,22 +781,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       }
       return fring + (size_t)stage * kT * kT;
     };
+    // (on a give-up q keeps pointing at the tile that was waited for, so the final
+    // drain covers it)
     auto release = [&]() -> bool {
       __syncthreads();
-      ++q;
       if (sh[1]) return false;
+      ++q;
       if (tid == 0 && pnext < 2 * ntile) issue();
       return true;
     };
     bool ok = true;
+    // this thread's 4 entries (rows e / 32, rhs e % 32, e = tid + 256 u) of block row b's
+    // gathered right-hand side, loaded one block row ahead
+    float pre[4];
+    auto fetch_rhs = [&](int b) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + kThreads * u, rr = e >> 5, k = e & 31, l = b * kT + rr;
+        pre[u] = (l < ni && k < R) ? (float)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]) : 0.f;
+      }
+    };
+    fetch_rhs(0);
     // forward sweep
     for (int b = 0; b < nbk && ok; ++b) {
-      for (int e = tid; e < kT * kT; e += kThreads) {
-        const int rr = e >> 5, k = e & 31, l = b * kT + rr;
-        float v = 0.f;
-        if (l < ni && k < R) v = (float)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]);
-        tin[swz(rr, k)] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + kThreads * u;
+        tin[swz(e >> 5, e & 31)] = pre[u];
       }
+      if (b + 1 < nbk) fetch_rhs(b + 1);
       __syncthreads();
       float c[4] = {0.f, 0.f, 0.f, 0.f};
       for (int t = tf[b]; t < b && ok; ++t) {
@@ -823,6 +842,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
     }
     // backward sweep
     for (int b = nbk - 1; b >= 0 && ok; --b) {
+      // the forward values of tile b - RING, which takes slot b % RING after this step
+      float4 refill = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b - RING >= 0) refill = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT)[tid];
       const float* D = wait_tile();
       float x[4] = {0.f, 0.f, 0.f, 0.f};
       tile_mma<true>(D, vring + (size_t)(b % RING) * kT * kT, x, mb, nb, g, t4);
@@ -854,9 +876,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
         ok = release();
       }
       if (ok && b - RING >= 0) {
-        const float4* sp = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT);
-        float4* vb = reinterpret_cast<float4*>(vring + (size_t)(b % RING) * kT * kT);
-        for (int e = tid; e < kT * kT / 4; e += kThreads) vb[e] = sp[e];
+        reinterpret_cast<float4*>(vring + (size_t)(b % RING) * kT * kT)[tid] = refill;
         __syncthreads();
       }
     }
