@@ -58,6 +58,24 @@ def parse():
     return ap.parse_args()
 
 
+def replica_env() -> tuple:
+    """(world, rank, local rank) from torchrun's environment; (1, 0, 0) when run alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over the replicas (the slowest replica sets the step time).  Works
+    on any initialised process group (NCCL with a device tensor, gloo on the CPU)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -188,9 +206,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -244,10 +260,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1) / args.steps
         if headline:
             clocks = ck.stop()
-        if world > 1:
-            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, world, dev)
         nl = sum(i["local_launches"] for i in infos)
         ms_local = sum(i["ms_local"] for i in infos) / max(nl, 1)
         its = sum(i["iters"] for i in infos)
