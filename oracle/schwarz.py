@@ -203,6 +203,17 @@ class TwoLevel:
         """M_additive^{-1} r = R_0^T C_00^{-1} R_0 r + sum_i R_i^T C_ii^{-1} R_i r (eq. (2.3))."""
         return self.apply_local(r) + self.apply_coarse(r)
 
+    def apply_balanced(self, A: sp.csr_matrix, r: np.ndarray) -> np.ndarray:
+        """The balanced two-level preconditioner of Section 2 (eq. balanced) applied to r:
+        Q r + (I - C Q)^T M_1 (I - C Q) r with Q = R_0^T C_00^{-1} R_0, the one-level
+        additive operator M_1 = sum_i R_i^T C_ii^{-1} R_i and C = A^T A applied as
+        A^T (A .).  (I - C Q)^T = I - Q C because C and Q are symmetric."""
+        def C(v):
+            return A.T @ (A @ v)
+        qr = self.apply_coarse(r)
+        u = self.apply_local(r - C(qr))
+        return qr + u - self.apply_coarse(C(u))
+
 
 def _band_lower(M: sp.spmatrix, bw: int) -> np.ndarray:
     """LAPACK lower banded storage: ab[d, j] = M[j + d, j] for d = 0..bw."""

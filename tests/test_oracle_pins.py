@@ -220,6 +220,37 @@ def test_condition_bound_theorem26(tiny):
     assert ev[-1] <= kc + 1 + 1e-9
 
 
+# --------------------------------------------------------------------------- balanced variant
+def test_balanced_variant(tiny):
+    """The balanced two-level operator of Section 2, Q + (I - CQ)^T M_1 (I - CQ), pinned by
+    what its definition implies (built with delta = 0 so that C_00 = R_0 C R_0^T exactly):
+    it is symmetric, it inverts C on the coarse space (M_bal C R_0^T = R_0^T, so M_bal C
+    has the eigenvalue 1 with multiplicity n_0), it conditions C better than the additive
+    operator (the paper's reason to use it), and PCG with it reaches the least-squares
+    solution."""
+    A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
+    M = O.build_two_level(A, tiny.part, tiny.nparts, tau=0.0, nev_max=16, delta_rel=0.0)
+    C = (A.T @ A).toarray()
+    R0T = M.R0T.toarray()
+    for j in range(0, R0T.shape[1], 7):
+        z = M.apply_balanced(A, C @ R0T[:, j])
+        assert np.linalg.norm(z - R0T[:, j]) <= 1e-10 * np.linalg.norm(R0T[:, j])
+    rng = np.random.default_rng(4)
+    x, y = rng.standard_normal(tiny.n), rng.standard_normal(tiny.n)
+    assert abs(M.apply_balanced(A, x) @ y - x @ M.apply_balanced(A, y)) <= 1e-12 * abs(x @ M.apply_balanced(A, y))
+    Mb = np.column_stack([M.apply_balanced(A, e) for e in np.eye(tiny.n)])
+    Ma = np.column_stack([M.apply(e) for e in np.eye(tiny.n)])
+    eb = sl.eigh(C, np.linalg.inv(0.5 * (Mb + Mb.T)), eigvals_only=True)
+    ea = sl.eigh(C, np.linalg.inv(0.5 * (Ma + Ma.T)), eigvals_only=True)
+    assert eb[0] > 0 and int(np.sum(np.abs(eb - 1.0) < 1e-8)) == M.n0
+    assert eb[-1] / eb[0] < ea[-1] / ea[0]
+    xb, ib = O.pcg(A, tiny.b, lambda r: M.apply_balanced(A, r), rtol=1e-12)
+    xl = np.linalg.lstsq(A.toarray(), tiny.b, rcond=None)[0]
+    assert np.linalg.norm(xb - xl) <= 1e-8 * np.linalg.norm(xl)
+    _, ia = O.pcg(A, tiny.b, M.apply, rtol=1e-12)
+    assert ib["iters"] < ia["iters"]
+
+
 # --------------------------------------------------------------------------- tau rule
 def test_auto_tau_and_cap(tiny):
     A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
