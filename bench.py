@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16"], help="headline form")
-    ap.add_argument("--forms", default="f32,f64", help="forms to run (comma list)")
+    ap.add_argument("--forms", default="f32,f64",
+                    help="forms to run (comma list of f32, f64, bf16; a trailing 'b' (f32b) selects the "
+                         "balanced second level instead of the additive one)")
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--nev", type=int, default=32)
@@ -234,19 +236,20 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    for form in forms:
+    for spec in forms:
+        form, variant = (spec[:-1], 1) if spec.endswith("b") else (spec, 0)
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
-                   nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000)
+                   nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()
         st = S.storage()
-        log(f"[bench] {form}: setup {setup_s:.2f}s (eig {sinfo['t_eig']:.2f}s) n0={sinfo['n0']} "
+        log(f"[bench] {spec}: setup {setup_s:.2f}s (eig {sinfo['t_eig']:.2f}s) n0={sinfo['n0']} "
             f"k in [{sinfo['kmin']},{sinfo['kmax']}] steps<= {sinfo['eig_steps_max']} fac={st['fac_elems']}")
         for _ in range(args.warmup):
             ls_solve(S.h, b_dev, 1, args.rtol, x_dev)
-        headline = form == args.prec
+        headline = spec == args.prec
         ck = None
         if headline:
             ck = Clocks(dev.index or 0)
@@ -270,7 +273,7 @@ def run_ours(args):
         loc_gbs = lb / (ms_local * 1e-3) / 1e9
         spmv_gbs = sb / (ms_spmv * 1e-3) / 1e9
         ms_iter = sum(i["ms_iter"] for i in infos) / max(its, 1)
-        results[form] = {
+        results[spec] = {
             "value": ms / 1000.0, "iterations": infos[-1]["iters"], "relres_true": infos[-1]["relres_true"],
             "ms_per_iteration_kernels": ms_iter, "lanes": [infos[-1]["lanes_csr"], infos[-1]["lanes_csc"]],
             "setup_s": setup_s, "eig_s": sinfo["t_eig"], "n0": sinfo["n0"], "kappa_lanczos": infos[-1]["kappa_lanczos"],

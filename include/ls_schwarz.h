@@ -81,6 +81,11 @@ typedef struct {
                           shifts delta and s of Section 4.1.2 it is not, and badly scaled
                           columns then see a shift far above their diagonal.  0 (the
                           default) follows the paper as written.                      */
+    int variant;       /* second level: 0 additive (eq. (2.3), the default); 1 balanced,
+                          Q + (I - CQ)^T M_1 (I - CQ) with Q = R_0^T C_00^{-1} R_0 and the
+                          one-level M_1 (Section 2): two more products with C and one
+                          more coarse correction per apply.  Single-problem handles and
+                          one right-hand side only (else LS_ERR_UNSUPPORTED).          */
 } ls_options;
 
 typedef struct {
@@ -111,7 +116,8 @@ typedef struct ls_handle ls_handle;
 
 /* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
- * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0. */
+ * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
+ * equilibrate = 0, variant = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping
@@ -197,7 +203,8 @@ ls_status ls_handle_info(const ls_handle* h, ls_info* info);
 /* ---- inspection calls used by tests and benchmarks ------------------------------ */
 
 /* z = M^{-1} r for one vector (host or device pointers, n entries each); which = 0:
- * the full two-level operator, 1: the local sum only, 2: the coarse term only.
+ * the full two-level operator (additive or balanced, as ls_options.variant selects),
+ * 1: the local sum only, 2: the coarse term Q r only.
  * Batched handles: LS_ERR_UNSUPPORTED. */
 ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int which);
 

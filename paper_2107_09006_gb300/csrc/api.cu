@@ -90,27 +90,81 @@ lsq::DotSite site(ls_handle* h, int slot, int counter, int out2 = 0) {
 }
 
 
+bool balanced(const ls_handle* h) { return h->opt.variant == 1 && h->coarse && h->n0 > 0; }
+
+// y = local solves of rin (and, with_coarse, the fused coarse restriction r0 = R_0 rin)
+void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
+  lsq::LocalArgs a{};
+  a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
+  a.blk_off = h->blk_off.p; a.blk_tf = h->blk_tf.p; a.blk_poff = h->blk_poff.p;
+  a.fac = h->prec == LS_PREC_F64 ? (const void*)h->L64.p
+        : h->prec == LS_PREC_F32 ? (const void*)h->L32.p : (const void*)h->L16.p;
+  a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
+  a.err = h->scal.p + lsq::S_ERR;
+  a.r = rin; a.y = h->ybuf.p;
+  a.coarse = with_coarse ? 1 : 0;
+  a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
+  a.Z = h->Z.p; a.r0 = h->r0.p;
+  lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, h->st);
+}
+
+// out = Q v = R_0^T C_00^{-1} R_0 v (restriction, dense coarse solve, prolongation)
+void coarse_term(ls_handle* h, const double* v, double* out) {
+  cudaStream_t st = h->st;
+  lsq::launch_restrict(h->N, h->int_off.p, h->int_glob.p, h->zoff.p, h->coff.p, h->Z.p, v, h->r0.p, st);
+  lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
+  lsq::ScatterArgs s{};
+  s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.coarse = 1; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
+  s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p;
+  s.z = out;
+  s.add_coarse_only = 1;
+  lsq::launch_scatter(s, st);
+}
+
+// out = C v = A^T (A v)
+void apply_C(ls_handle* h, const double* v, double* out) {
+  lsq::launch_spmv_csr(csr(h), v, h->q.p, h->lanes_csr, h->grid_csr, h->st);
+  lsq::launch_spmv_csc(csc(h), h->q.p, out, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, h->st);
+}
+
+// Kernels of one apply of the balanced operator (see precond_balanced).
+constexpr int kBalancedLaunches = 14;
+
+// z = Q r + (I - Q C) M_1 (I - C Q) r (the balanced two-level operator of Section 2)
+// with the fused dots r.z (and r_old.z).
+void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, bool flex, bool timed) {
+  cudaStream_t st = h->st;
+  coarse_term(h, rin, h->bal_y.p);                                     // Q r
+  apply_C(h, h->bal_y.p, h->bal_t.p);                                  // C Q r
+  lsq::launch_axpby(h->n, 1.0, rin, -1.0, h->bal_t.p, h->bal_t.p, st);  // t = (I - CQ) r
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  launch_local(h, h->bal_t.p, false);
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  lsq::ScatterArgs s{};
+  s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.z = h->bal_u.p;
+  s.add_coarse_only = 2;
+  lsq::launch_scatter(s, st);                                          // u = M_1 t
+  apply_C(h, h->bal_u.p, h->bal_t.p);                                  // C u
+  coarse_term(h, h->bal_t.p, h->bal_v.p);                              // Q C u
+  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  lsq::launch_combine3(h->n, h->bal_y.p, h->bal_u.p, h->bal_v.p, zout, rin, flex ? h->r_old.p : nullptr,
+                       dots ? site(h, lsq::S_RZ, 2, lsq::S_RZO - lsq::S_RZ) : lsq::DotSite{}, st);
+}
+
 // z = M^{-1} r (which: 0 both terms, 1 local only, 2 coarse only) with the fused dots
 // r.z (and r_old.z for the flexible recurrence) into the partial arrays.
 void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots, bool flex, bool timed = false) {
   cudaStream_t st = h->st;
+  if (which == 0 && balanced(h)) {
+    precond_balanced(h, rin, zout, dots, flex, timed);
+    return;
+  }
   if (which != 0 && which != 1) throw LsError(LS_ERR_INVALID, "precond: which must be 0 or 1");
   if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
   const bool use_coarse = h->coarse && h->n0 > 0 && which != 1;
-  if (which != 2) {
-    lsq::LocalArgs a{};
-    a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
-    a.blk_off = h->blk_off.p; a.blk_tf = h->blk_tf.p; a.blk_poff = h->blk_poff.p;
-    a.fac = h->prec == LS_PREC_F64 ? (const void*)h->L64.p
-          : h->prec == LS_PREC_F32 ? (const void*)h->L32.p : (const void*)h->L16.p;
-    a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
-    a.err = h->scal.p + lsq::S_ERR;
-    a.r = rin; a.y = h->ybuf.p;
-    a.coarse = use_coarse ? 1 : 0;
-    a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
-    a.Z = h->Z.p; a.r0 = h->r0.p;
-    lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, st);
-  }
+  if (which != 2) launch_local(h, rin, use_coarse);
   if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
   if (use_coarse) lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
   if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
@@ -126,7 +180,10 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
 
 // One PCG iteration: w = A^T (A p), alpha, x, r, z = M^{-1} r, beta, p.
 // Kernels one iteration launches (for the launch count reported in ls_info).
-int iteration_launches(const ls_handle* h) { return 6 + ((h->coarse && h->n0 > 0) ? 1 : 0); }
+int iteration_launches(const ls_handle* h) {
+  if (balanced(h)) return 4 + kBalancedLaunches;
+  return 6 + ((h->coarse && h->n0 > 0) ? 1 : 0);
+}
 
 void iteration(ls_handle* h, bool flex) {
   cudaStream_t st = h->st;
@@ -787,6 +844,9 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->r0.alloc(std::max<int64_t>(h->n0p, 1)); h->r0.zero(st);
   h->y0.alloc(std::max<int64_t>(h->n0p, 1)); h->y0.zero(st);
   h->tv.alloc(h->n); h->bv.alloc(h->m);
+  if (h->opt.variant == 1) {
+    h->bal_y.alloc(h->n); h->bal_t.alloc(h->n); h->bal_u.alloc(h->n); h->bal_v.alloc(h->n);
+  }
   h->parts.alloc(2 * (size_t)lsq::kMaxGrid);
   h->counters.alloc(8); h->counters.zero(st);
   h->scal.alloc(lsq::S_NSLOT); h->scal.zero(st);
@@ -822,6 +882,7 @@ void ls_default_options(ls_options* o) {
   o->use_graph = 1;
   o->time_kernels = 0;
   o->equilibrate = 0;
+  o->variant = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -844,6 +905,9 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.factor_prec < 0 || h->opt.factor_prec > 2) throw LsError(LS_ERR_INVALID, "bad factor_prec");
     if (h->opt.maxit < 1 && h->opt.fixed_iters < 1) throw LsError(LS_ERR_INVALID, "maxit must be positive");
     if (h->opt.nev_max < 0) throw LsError(LS_ERR_INVALID, "nev_max must be >= 0");
+    if (h->opt.variant < 0 || h->opt.variant > 1) throw LsError(LS_ERR_INVALID, "variant must be 0 or 1");
+    if (h->opt.variant == 1 && nprob > 1)
+      throw LsError(LS_ERR_UNSUPPORTED, "the balanced variant is implemented for single-problem handles");
     if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
     CK(cudaGetDevice(&h->dev));
     if (stream) {
@@ -987,14 +1051,9 @@ ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int 
     CK(cudaSetDevice(h->dev));
     CK(cudaMemcpyAsync(h->tv.p, r, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     if (which == 2) {
-      // coarse term alone: run the local kernel for the restriction, then keep only the coarse part
-      precond(h, h->tv.p, h->w.p, 0, false, false);
-      lsq::ScatterArgs s{};
-      s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
-      s.coarse = (h->coarse && h->n0 > 0) ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
-      s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p; s.r = h->tv.p; s.z = h->w.p;
-      s.add_coarse_only = 1;
-      lsq::launch_scatter(s, h->st);
+      // the coarse term Q r alone
+      if (h->coarse && h->n0 > 0) coarse_term(h, h->tv.p, h->w.p);
+      else CK(cudaMemsetAsync(h->w.p, 0, sizeof(double) * h->n, h->st));
     } else {
       precond(h, h->tv.p, h->w.p, which, false, false);
     }

@@ -241,6 +241,8 @@ ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double*
   BlockState& B = h->blk;
   cudaStream_t st = h->st;
   if (R < 1 || R > 32) throw LsError(LS_ERR_UNSUPPORTED, "the multi right-hand-side path takes 1 to 32 right-hand sides");
+  if (h->opt.variant != 0)
+    throw LsError(LS_ERR_UNSUPPORTED, "the multi right-hand-side path applies the additive two-level operator");
   if (!B.local_ok)
     throw LsError(LS_ERR_UNSUPPORTED, "the widest local factor block row (" + std::to_string(B.ring) +
                                           " tiles) does not fit the multi right-hand-side local solve");

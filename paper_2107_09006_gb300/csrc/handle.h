@@ -152,6 +152,7 @@ struct ls_handle {
   DevBuf<double> Z, Xinv;
 
   DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
+  DevBuf<double> bal_y, bal_t, bal_u, bal_v;  // work vectors of the balanced variant
   DevBuf<double> parts, scal, ahist, bhist;
   DevBuf<unsigned> counters;  // ticket counters of the fused reductions
   DevBuf<int> ctr;

@@ -285,6 +285,44 @@ __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
   if (a.dots.parts) finish_dots(acc_rz, acc_rzo, a.r_old != nullptr, a.dots);
 }
 
+// r0[c0 + t] = sum_jj Zbar_i[t, jj] v[Omega_I,i[jj]] (one block per subdomain, one warp
+// per coarse vector): the coarse restriction R_0 v on its own.
+__global__ void __launch_bounds__(kThreads) k_restrict(const int64_t* __restrict__ int_off,
+                                                       const int32_t* __restrict__ int_glob,
+                                                       const int64_t* __restrict__ zoff,
+                                                       const int32_t* __restrict__ coff, const double* __restrict__ Z,
+                                                       const double* __restrict__ v, double* __restrict__ r0) {
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c0 = coff[i], kk = coff[i + 1] - c0;
+  const int64_t io = int_off[i];
+  const int64_t nIi = int_off[i + 1] - io;
+  const double* Zi = Z + zoff[i];
+  for (int t = w; t < kk; t += kWarps) {
+    double acc = 0.0;
+    for (int64_t jj = lane; jj < nIi; jj += 32) acc += Zi[(int64_t)t * nIi + jj] * v[int_glob[io + jj]];
+    acc = warp_sum(acc);
+    if (lane == 0) r0[c0 + t] = acc;
+  }
+}
+
+// z = a + b - c with the fused dots r.z (and r_old.z) of the preconditioned residual.
+__global__ void __launch_bounds__(kThreads) k_combine3(int64_t n, const double* __restrict__ a,
+                                                       const double* __restrict__ b, const double* __restrict__ c,
+                                                       double* __restrict__ z, const double* __restrict__ r,
+                                                       const double* __restrict__ r_old, DotSite ds) {
+  double d1 = 0.0, d2 = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[k] + b[k] - c[k];
+    z[k] = v;
+    if (ds.parts) {
+      d1 += r[k] * v;
+      if (r_old) d2 += r_old[k] * v;
+    }
+  }
+  if (ds.parts) finish_dots(d1, d2, r_old != nullptr, ds);
+}
+
 // y0 = X r0 for the dense n0 x n0 coarse inverse (one warp per row).
 __global__ void __launch_bounds__(kThreads) k_gemv(int64_t n0, const double* __restrict__ X,
                                                    const double* __restrict__ r0, double* __restrict__ y0) {
@@ -411,6 +449,16 @@ void launch_gather64(int64_t n, const int64_t* idx, const double* src, double* d
 void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,
                         int accumulate, cudaStream_t st) {
   k_scatter_idx<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx32, idx64, src, dst, accumulate);
+}
+
+void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,
+                     const double* Z, const double* v, double* r0, cudaStream_t st) {
+  k_restrict<<<N, kThreads, 0, st>>>(int_off, int_glob, zoff, coff, Z, v, r0);
+}
+
+void launch_combine3(int64_t n, const double* a, const double* b, const double* c, double* z, const double* r,
+                     const double* r_old, const DotSite& ds, cudaStream_t st) {
+  k_combine3<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, a, b, c, z, r, r_old, ds);
 }
 
 void launch_scatter(const ScatterArgs& a, cudaStream_t st) {

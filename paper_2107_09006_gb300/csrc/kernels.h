@@ -69,6 +69,12 @@ struct ScatterArgs {
   int add_coarse_only;  // 1: z = coarse term only; 2: z = local sum only
 };
 void launch_scatter(const ScatterArgs& a, cudaStream_t st);
+// r0 = R_0 v (coarse restriction alone, FP64)
+void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,
+                     const double* Z, const double* v, double* r0, cudaStream_t st);
+// z = a + b - c with r.z -> ds.out[0] and (r_old != nullptr) r_old.z -> ds.out[ds.out2]
+void launch_combine3(int64_t n, const double* a, const double* b, const double* c, double* z, const double* r,
+                     const double* r_old, const DotSite& ds, cudaStream_t st);
 void launch_gemv(int64_t n0, const double* X, const double* r0, double* y0, cudaStream_t st);
 void launch_grad_vals(const CsrDev& A, const double* rho, const double* lam, const double* mu,
                       const double* x, double* g, int accumulate, cudaStream_t st);
