@@ -51,10 +51,14 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-side", type=int, default=256, help="grid side of the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision", "batch", "tausweep"],
                     help="solve: the timed benchmark line; nsweep: iterations/setup vs subdomain count "
                          "(blocks 128/64/32); precision: errors of every form on the column-scaled workload; "
-                         "batch: 64 independent problems x 32 right-hand sides in shared launches")
+                         "batch: 64 independent problems x 32 right-hand sides in shared launches; "
+                         "tausweep: iterations and n0 against the threshold tau")
+    ap.add_argument("--zero-sum", action="store_true",
+                    help="nsweep/tausweep on the zero-sum variant of the grid workload (random rows centred to "
+                         "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
     ap.add_argument("--nprob", type=int, default=64)
     ap.add_argument("--nrhs", type=int, default=32)
     return ap.parse_args()
@@ -351,13 +355,29 @@ def _device_setup():
 def run_nsweep(args):
     """Subdomain-count sweep on the n = 1M grid: for blocks of 128, 64 and 32 columns a
     side (N = 64, 256, 1024) the setup split (index sets + factors, eigensolve + coarse),
-    n0, iterations to rtol and the solve time; one JSON line per N and a summary."""
+    n0, iterations to rtol and the solve time of the two-level additive form, plus the
+    iterations of the one-level method and of the balanced form; one JSON line per N and
+    a summary."""
     torch, dev = _device_setup()
     from paper_2107_09006_gb300 import Solver, ls_solve
     from workloads import config_scale
     rows = []
+
+    def iters_of(P, b, x, stream, **kw):
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   factor_prec=args.prec, maxit=5000, **kw)
+        info = ls_solve(S.h, b, 1, args.rtol, x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ls_solve(S.h, b, 1, args.rtol, x)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        S.close()
+        torch.cuda.empty_cache()
+        return info["iters"], info["kappa_lanczos"], e0.elapsed_time(e1) / 1000.0
+
     for block in (128, 64, 32):
-        P = config_scale(side=args.side, block=block)
+        P = config_scale(side=args.side, block=block, zero_sum=args.zero_sum)
         b = torch.as_tensor(P.b, device=dev)
         x = torch.empty(P.n, dtype=torch.float64, device=dev)
         stream = torch.cuda.current_stream(dev)
@@ -384,14 +404,18 @@ def run_nsweep(args):
                "solve_s": statistics.median(ts), "ms_local": it["ms_local"] / max(it["local_launches"], 1),
                "ms_coarse_per_iter": it["ms_coarse"] / max(it["iters"], 1),
                "ms_spmv_per_iter": it["ms_spmv"] / max(it["iters"], 1), "fac_elems": S.storage()["fac_elems"]}
-        log(f"[nsweep] {json.dumps(row)}")
-        rows.append(row)
         S.close()
         del S
         torch.cuda.empty_cache()
+        i1, k1, s1 = iters_of(P, b, x, stream, coarse=0, nev_max=0)
+        ib, kb, sb = iters_of(P, b, x, stream, nev_max=args.nev, variant=1)
+        row.update({"one_level": {"iterations": i1, "kappa_lanczos": k1, "solve_s": s1},
+                    "balanced": {"iterations": ib, "kappa_lanczos": kb, "solve_s": sb}})
+        log(f"[nsweep] {json.dumps(row)}")
+        rows.append(row)
     its = [r["iterations"] for r in rows]
-    print(json.dumps({"report": "nsweep", "workload": f"grid{args.side}-r3k8, nev_max {args.nev}, tau auto, "
-                      f"form {args.prec}, rtol {args.rtol:g}", "rows": rows,
+    print(json.dumps({"report": "nsweep", "workload": f"grid{args.side}-r3k8" + ("-zerosum" if args.zero_sum else "") +
+                      f", nev_max {args.nev}, tau auto, form {args.prec}, rtol {args.rtol:g}", "rows": rows,
                       "iterations_max_over_min": max(its) / min(its)}), flush=True)
 
 
@@ -450,6 +474,48 @@ def run_precision(args):
                       "reference": {"form": "f64", "construction": "equilibrated", "rtol": 1e-13,
                                     "iterations": iref["iters"], "relres_true": iref["relres_true"]},
                       "rows": rows}), flush=True)
+
+
+def run_tausweep(args):
+    """Threshold sweep on the n = 1M grid (256 subdomains, FP32 factors, at most 64
+    vectors per subdomain): the one-level method, then for each tau the coarse dimension
+    n0 and the iterations and solve time of the additive and balanced two-level forms
+    (the analogue of the paper's iterations / n0 versus tau study)."""
+    torch, dev = _device_setup()
+    from paper_2107_09006_gb300 import Solver, ls_solve
+    from workloads import config_scale
+    P = config_scale(side=args.side, block=args.block, zero_sum=args.zero_sum)
+    b = torch.as_tensor(P.b, device=dev)
+    x = torch.empty(P.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+
+    def run(label, tau_label, **kw):
+        t = time.time()
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   factor_prec=args.prec, maxit=3000, **kw)
+        torch.cuda.synchronize(dev)
+        setup = time.time() - t
+        ls_solve(S.h, b, 1, args.rtol, x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ls_solve(S.h, b, 1, args.rtol, x)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        si = S.info()
+        row = {"form": label, "tau": tau_label, "n0": si["n0"], "kmax": si["kmax"], "iterations": info["iters"],
+               "kappa_lanczos": info["kappa_lanczos"], "solve_s": e0.elapsed_time(e1) / 1000.0, "setup_s": setup}
+        log(f"[tausweep] {json.dumps(row)}")
+        rows.append(row)
+        S.close()
+        torch.cuda.empty_cache()
+
+    run("one-level", None, coarse=0, nev_max=0)
+    for tau in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.8):
+        for variant, label in ((0, "additive"), (1, "balanced")):
+            run(label, tau, tau=tau, nev_max=64, variant=variant)
+    print(json.dumps({"report": "tausweep", "workload": f"{P.name}, form {args.prec}, "
+                      f"rtol {args.rtol:g}, nev_max 64", "rows": rows}), flush=True)
 
 
 def run_batch(args):
@@ -542,5 +608,7 @@ if __name__ == "__main__":
         run_precision(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "tausweep":
+        run_tausweep(a)
     else:
         run_ours(a)

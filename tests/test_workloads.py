@@ -64,3 +64,15 @@ def test_batched_block_diagonal():
         m, n, rp, c, v, part, N, b = B.problem(q)
         assert m == 5 * n and rp[0] == 0 and c.max() < n and part.max() == N - 1 and b.shape == (2, m)
     assert nid == B.nparts
+
+
+def test_zero_sum_rows():
+    """The zero-sum variant takes the same draws and centres each random row."""
+    m, n, rp, c, v, b, _ = make_grid_ls(20, 20, 4, 6, 2, 3)
+    m2, n2, rp2, c2, v2, b2, _ = make_grid_ls(20, 20, 4, 6, 2, 3, zero_sum=True)
+    assert np.array_equal(c, c2) and np.array_equal(b, b2)
+    k = 6
+    vr, vr2 = v[: 4 * n * k].reshape(-1, k), v2[: 4 * n * k].reshape(-1, k)
+    assert np.allclose(vr2.sum(axis=1), 0.0, atol=1e-12)
+    assert np.allclose(vr2, vr - vr.mean(axis=1, keepdims=True))
+    assert np.array_equal(v[4 * n * k:], v2[4 * n * k:])

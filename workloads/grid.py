@@ -66,11 +66,17 @@ def _window_offsets(radius: int):
 
 def make_grid_ls(W: int, H: int, rows_per_point: int, k: int, radius: int, seed: int,
                  ident_scale: float = 1e-2, col_scale: bool = False, nrhs: int = 1,
-                 with_xstar: bool = False, name: str = "") -> tuple:
+                 with_xstar: bool = False, name: str = "", zero_sum: bool = False) -> tuple:
     """Draw the CSR matrix, right-hand side(s) and optional x* of one grid problem.
 
     Returns ``(m, n, row_ptr, col, val, b, xstar)``; ``b`` has shape ``[m]`` when
     ``nrhs == 1`` else ``[nrhs, m]`` (one right-hand side per row).
+
+    ``zero_sum``: the values of every random row are centred to sum to zero (the same
+    draws, minus their row mean).  Every random row then annihilates constant vectors,
+    so C = A^T A behaves like a graph Laplacian whose near null space (smooth, slowly
+    varying vectors) is lifted only by the 1e-2 I rows: a hard case for one-level
+    Schwarz, which the coarse space is there to fix.
     """
     n = W * H
     m_rand = rows_per_point * n
@@ -95,6 +101,8 @@ def make_grid_ls(W: int, H: int, rows_per_point: int, k: int, radius: int, seed:
         py = np.take_along_axis(gy, pick, axis=1)
         cols[s:e] = np.sort(py * W + px, axis=1)
     vals = rng.standard_normal((m_rand, k))
+    if zero_sum:
+        vals = vals - vals.mean(axis=1, keepdims=True)
 
     row_ptr = np.empty(m + 1, dtype=np.int64)
     row_ptr[: m_rand + 1] = np.arange(m_rand + 1, dtype=np.int64) * k
@@ -168,15 +176,16 @@ def config_tiny(seed: int = 0) -> GridLS:
 
 
 def config_scale(side: int = 1024, block: int = 64, seed: int = 0, col_scale: bool = False,
-                 name: str | None = None) -> GridLS:
+                 name: str | None = None, zero_sum: bool = False) -> GridLS:
     """Grid side x side, 4n rows of 8 nonzeros (radius 3) + 1e-2 I, square block subdomains.
 
     side = 1024, block = 64 is the n = 1,048,576 / 256-subdomain workload; block 128
     and 32 give 64 and 1024 subdomains.
     """
     W = H = side
-    m, n, rp, c, v, b, xs = make_grid_ls(W, H, 4, 8, 3, seed, col_scale=col_scale)
-    nm = name or f"grid{side}-r3k8-N{(side // block) ** 2}" + ("-colscale" if col_scale else "")
+    m, n, rp, c, v, b, xs = make_grid_ls(W, H, 4, 8, 3, seed, col_scale=col_scale, zero_sum=zero_sum)
+    nm = name or f"grid{side}-r3k8-N{(side // block) ** 2}" + ("-colscale" if col_scale else "") + \
+        ("-zerosum" if zero_sum else "")
     return _pack(nm, W, H, m, n, rp, c, v, b, xs, block_partition(W, H, block, block))
 
 
