@@ -28,6 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "n=1M LS solve s to 1e-8 normal-eq rel resid, mixed vs FP64 form; apply HBM GB/s"
+# DRAM bytes (read + write) of one k_local_solve launch, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one pass) on the workload
+# and form named in the key; valid while that kernel and workload stay as they are.
+LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32"): 5.80e9 + 8.57e6}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -318,7 +322,8 @@ def run_ours(args):
                                                 "f64": "plain FP64", "bf16": "mixed: BF16 local factors"}[args.prec],
                    "l2": "inputs larger than L2 (factors alone exceed 129 MB)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": head["local_solve"]["GBps"], "peak": hbm_peak, "unit": "GB/s",
-                     "frac": head["local_solve"]["frac"], "traffic": None,
+                     "frac": head["local_solve"]["frac"],
+                     "traffic": LOCAL_SOLVE_TRAFFIC.get((P.name, args.prec)),
                      "kernel": "k_local_solve (batched envelope trisolves, one CTA per subdomain)",
                      "bytes_per_launch": head["local_solve"]["bytes_per_launch"],
                      "ms_per_launch": head["local_solve"]["ms_per_launch"], "peak_source": peak_src},
