@@ -35,6 +35,8 @@ from .schwarz import (  # noqa: F401
     pcg,
     flexible_pcg,
     lanczos_kappa,
+    preconditioned_lsqr,
+    lsqr_kappa,
     adjoint_gradient,
     multiplicity_km,
     colouring_kc,

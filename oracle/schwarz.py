@@ -379,6 +379,98 @@ def pcg(A: sp.csr_matrix, b: np.ndarray, apply_M, rtol: float = 1e-8, maxit: int
     return x, dict(iters=it, relres_true=relres_true, alphas=alphas, betas=betas, hist=hist)
 
 
+def preconditioned_lsqr(A: sp.csr_matrix, b: np.ndarray, apply_M, rtol: float = 1e-8, maxit: int = 1000,
+                        fixed_iters: int | None = None, check_factor: float = 10.0):
+    """LSQR with a symmetric positive definite preconditioner applied as z = M^{-1} s, the
+    outer solver the paper uses (Section 4.1.3: left-preconditioned LSQR, which needs
+    only applications of M^{-1}).
+
+    Golub-Kahan bidiagonalization of A between R^m (Euclidean) and R^n with the inner
+    product <x, y> = x^T M y, in which the adjoint of A is M^{-1} A^T:
+        beta_1 u_1 = b,  alpha_1 v_1 = M^{-1} A^T u_1,
+        beta_{k+1} u_{k+1} = A v_k - alpha_k u_k,
+        alpha_{k+1} v_{k+1} = M^{-1} A^T u_{k+1} - beta_{k+1} v_k,
+    where the M-norm alpha = (s^T M^{-1} s)^{1/2} of s = A^T u - beta M v is computed
+    from s and t = M^{-1} s (M v is carried along as q = s / alpha).  The least-squares
+    problem min ||beta_1 e_1 - B_k y|| is solved by the usual plane rotations, so
+    x_k = V_k y_k minimises ||b - A x|| over the Krylov space of M^{-1} A^T A started
+    from M^{-1} A^T b: the same iterates as PCG on the normal equations in exact
+    arithmetic.
+
+    Stopping: the configs' test ||A^T (b - A x)|| <= rtol ||A^T b||, evaluated on the
+    true residual from the first iteration at which LSQR's own estimate of the
+    preconditioned normal residual, ||M^{-1} A^T r_k||_M = phibar_{k+1} alpha_{k+1} |c_k|,
+    has fallen below check_factor * rtol times its initial value alpha_1 beta_1.
+    With ``fixed_iters`` it runs exactly that many iterations.
+    Returns x and a dict with iterations, the true relative residual and the
+    bidiagonal entries (alphas, betas).
+    """
+    At = A.T.tocsr()
+    gn = np.linalg.norm(At @ b)
+    n = A.shape[1]
+    x = np.zeros(n)
+    beta = np.linalg.norm(b)
+    if beta == 0.0 or gn == 0.0:
+        return x, dict(iters=0, relres_true=0.0, alphas=[], betas=[])
+    u = b / beta
+    s = At @ u
+    t = apply_M(s)
+    alpha = np.sqrt(s @ t)
+    v, q = t / alpha, s / alpha
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    est0 = alpha * beta
+    alphas, betas = [alpha], [beta]
+    it = 0
+    checking = False
+    while True:
+        if fixed_iters is not None and it >= fixed_iters:
+            break
+        if fixed_iters is None and it >= maxit:
+            break
+        u = A @ v - alpha * u
+        beta = np.linalg.norm(u)
+        u = u / beta
+        s = At @ u - beta * q
+        t = apply_M(s)
+        alpha = np.sqrt(s @ t)
+        v, q = t / alpha, s / alpha
+        rho = np.hypot(rhobar, beta)
+        c, sn = rhobar / rho, beta / rho
+        theta = sn * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = sn * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        it += 1
+        alphas.append(alpha)
+        betas.append(beta)
+        if fixed_iters is None:
+            if not checking and phibar * alpha * abs(c) <= check_factor * rtol * est0:
+                checking = True
+            if checking and np.linalg.norm(At @ (b - A @ x)) <= rtol * gn:
+                break
+    relres_true = np.linalg.norm(At @ (b - A @ x)) / gn
+    return x, dict(iters=it, relres_true=relres_true, alphas=alphas, betas=betas)
+
+
+def lsqr_kappa(alphas, betas) -> float:
+    """kappa of M^{-1} A^T A estimated from the bidiagonal: the Lanczos matrix of the
+    normal-equations operator is B_k^T B_k, with diagonal alpha_j^2 + beta_{j+1}^2 and
+    off-diagonal alpha_{j+1} beta_{j+1} (alphas[0] = alpha_1, betas[0] = beta_1)."""
+    k = len(alphas) - 1
+    if k < 1:
+        return 0.0
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = alphas[j] ** 2 + betas[j + 1] ** 2
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = alphas[j + 1] * betas[j + 1]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[-1] / ev[0])
+
+
 def flexible_pcg(A: sp.csr_matrix, b: np.ndarray, apply_M, rtol: float = 1e-8,
                  maxit: int = 1000, fixed_iters: int | None = None):
     """Flexible PCG: beta = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k) (Polak-Ribiere form),

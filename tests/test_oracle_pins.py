@@ -251,6 +251,32 @@ def test_balanced_variant(tiny):
     assert ib["iters"] < ia["iters"]
 
 
+# --------------------------------------------------------------------------- preconditioned LSQR
+def test_preconditioned_lsqr(tiny):
+    """The LSQR outer solver: with M = I it is textbook LSQR (scipy's iterates); with the
+    two-level operator its iterates are PCG's on the normal equations (both minimise
+    ||b - A x|| over the same Krylov space), its bidiagonal gives PCG's Lanczos kappa,
+    and it reaches the least-squares solution."""
+    import scipy.sparse.linalg as sla
+    A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
+    for k in (1, 3, 6):
+        x, _ = O.preconditioned_lsqr(A, tiny.b, lambda v: v, fixed_iters=k)
+        xs = sla.lsqr(A, tiny.b, atol=0, btol=0, conlim=0, iter_lim=k)[0]
+        assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+    M = O.build_two_level(A, tiny.part, tiny.nparts, tau=0.0, nev_max=16)
+    for k in (1, 6, 10):
+        xl, _ = O.preconditioned_lsqr(A, tiny.b, M.apply, fixed_iters=k)
+        xp, _ = O.pcg(A, tiny.b, M.apply, fixed_iters=k)
+        assert np.linalg.norm(xl - xp) <= 1e-10 * np.linalg.norm(xp)
+    xl, il = O.preconditioned_lsqr(A, tiny.b, M.apply, rtol=1e-10)
+    _, ip = O.pcg(A, tiny.b, M.apply, rtol=1e-10)
+    assert il["relres_true"] <= 1e-10 and abs(il["iters"] - ip["iters"]) <= 1
+    xd = np.linalg.lstsq(A.toarray(), tiny.b, rcond=None)[0]
+    assert np.linalg.norm(xl - xd) <= 1e-6 * np.linalg.norm(xd)
+    kl, kp = O.lsqr_kappa(il["alphas"], il["betas"]), O.lanczos_kappa(ip["alphas"], ip["betas"])
+    assert abs(kl - kp) <= 1e-6 * kp
+
+
 # --------------------------------------------------------------------------- tau rule
 def test_auto_tau_and_cap(tiny):
     A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
