@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16"], help="headline form")
     ap.add_argument("--forms", default="f32,f64",
-                    help="forms to run (comma list of f32, f64, bf16; a trailing 'b' (f32b) selects the "
-                         "balanced second level instead of the additive one)")
+                    help="forms to run (comma list of f32, f64, bf16; suffix 'b' (f32b) selects the balanced "
+                         "second level instead of the additive one, suffix 'l' (f32l, f32bl) the LSQR outer "
+                         "solver instead of PCG)")
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--nev", type=int, default=32)
@@ -245,10 +246,13 @@ def run_ours(args):
             dist.barrier()
 
     for spec in forms:
-        form, variant = (spec[:-1], 1) if spec.endswith("b") else (spec, 0)
+        form = spec.rstrip("bl")
+        variant = 1 if "b" in spec[len(form):] else 0
+        solver = 1 if "l" in spec[len(form):] else 0
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
-                   nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant)
+                   nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,
+                   solver=solver)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()

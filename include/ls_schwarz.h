@@ -86,6 +86,12 @@ typedef struct {
                           one-level M_1 (Section 2): two more products with C and one
                           more coarse correction per apply.  Single-problem handles and
                           one right-hand side only (else LS_ERR_UNSUPPORTED).          */
+    int solver;        /* outer Krylov method of ls_solve: 0 PCG on the normal equations
+                          (the default); 1 LSQR preconditioned with M^{-1} (the paper's
+                          solver, Section 4.1.3): Golub-Kahan bidiagonalization in the
+                          inner product of M, one preconditioner apply per iteration,
+                          the same stopping test on the true residual.  Single problem,
+                          one right-hand side; ls_backward always uses PCG.           */
 } ls_options;
 
 typedef struct {
@@ -117,7 +123,7 @@ typedef struct ls_handle ls_handle;
 /* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
- * equilibrate = 0, variant = 0. */
+ * equilibrate = 0, variant = 0, solver = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping

@@ -138,9 +138,9 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
   coarse_term(h, rin, h->bal_y.p);                                     // Q r
   apply_C(h, h->bal_y.p, h->bal_t.p);                                  // C Q r
   lsq::launch_axpby(h->n, 1.0, rin, -1.0, h->bal_t.p, h->bal_t.p, st);  // t = (I - CQ) r
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[2], st);
   launch_local(h, h->bal_t.p, false);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[3], st);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
   s.z = h->bal_u.p;
@@ -148,7 +148,7 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
   lsq::launch_scatter(s, st);                                          // u = M_1 t
   apply_C(h, h->bal_u.p, h->bal_t.p);                                  // C u
   coarse_term(h, h->bal_t.p, h->bal_v.p);                              // Q C u
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[4], st);
   lsq::launch_combine3(h->n, h->bal_y.p, h->bal_u.p, h->bal_v.p, zout, rin, flex ? h->r_old.p : nullptr,
                        dots ? site(h, lsq::S_RZ, 2, lsq::S_RZO - lsq::S_RZ) : lsq::DotSite{}, st);
 }
@@ -162,12 +162,12 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
     return;
   }
   if (which != 0 && which != 1) throw LsError(LS_ERR_INVALID, "precond: which must be 0 or 1");
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[2], st);
   const bool use_coarse = h->coarse && h->n0 > 0 && which != 1;
   if (which != 2) launch_local(h, rin, use_coarse);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[3], st);
   if (use_coarse) lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[4], st);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
   s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
@@ -188,15 +188,15 @@ int iteration_launches(const ls_handle* h) {
 void iteration(ls_handle* h, bool flex) {
   cudaStream_t st = h->st;
   const bool timed = h->opt.time_kernels != 0;
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[0], st);
   lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, h->grid_csr, st);
   lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, site(h, lsq::S_PW, 0), h->lanes_csc, h->grid_csc, st);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[1], st);
   lsq::launch_cg_update(h->n, h->scal.p, h->p.p, h->w.p, h->x.p, h->r.p, flex ? h->r_old.p : nullptr,
                         site(h, lsq::S_RR, 1), h->ctr.p, h->ahist.p, h->hist_cap, st);
   precond(h, h->r.p, h->z.p, 0, true, flex, timed);
   lsq::launch_p_update(h->n, h->scal.p, h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, flex ? 1 : 0, st);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[5], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[5], st);
   CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
 }
 
@@ -357,6 +357,144 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     return (g_err = "maximum number of iterations reached, true relative residual " +
                     std::to_string(inf.relres_true), LS_ERR_NOT_CONVERGED);
   return LS_OK;
+}
+
+// Preconditioned LSQR on min ||A' x - b'|| (b' in h->bv, result in h->x): Golub-Kahan
+// bidiagonalization between R^m and R^n with the inner product of M, so the adjoint of
+// A is M^{-1} A^T and each step applies the preconditioner once (Section 4.1.3 uses
+// left-preconditioned LSQR); the plane-rotation recurrences run on the host, the vector
+// work on the device.  Stopping: the true residual test ||A^T (b - A x)|| <= rtol ||A^T b||,
+// evaluated from the first step at which LSQR's estimate of ||M^{-1} A^T r||_M has
+// fallen below 10 rtol times its initial value.
+ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n, m = h->m;
+  const double t0 = now_s();
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
+  lsq::launch_spmv_csc(csc(h), h->bv.p, h->r.p, nullptr, site(h, lsq::S_TMP, 0), h->lanes_csc, h->grid_csc, st);
+  const double gg = dev_sum(h);
+  lsq::launch_dot(m, h->bv.p, h->bv.p, site(h, lsq::S_TMP, 3), st);
+  const double bb = dev_sum(h);
+  launches += 2;
+  if (!std::isfinite(gg) || !std::isfinite(bb)) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
+  const double gn = std::sqrt(gg);
+  lsq::launch_fill(n, 0.0, h->x.p, st);
+  launches += 1;
+  CK(cudaMemsetAsync(h->scal.p, 0, sizeof(double) * lsq::S_NSLOT, st));
+  auto finish = [&](int it, bool converged, double rel) -> ls_status {
+    inf.iters = it;
+    inf.relres_true = rel;
+    inf.relres_recursive = rel;
+    inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
+    inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
+    inf.eig_steps_max = h->sinfo.eig_steps_max;
+    inf.launches = launches;
+    inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+    inf.t_solve = now_s() - t0;
+    if (info) *info = inf;
+    if (!converged && h->opt.fixed_iters <= 0)
+      return (g_err = "maximum number of iterations reached, true relative residual " + std::to_string(rel),
+              LS_ERR_NOT_CONVERGED);
+    return LS_OK;
+  };
+  if (gn == 0.0 || bb == 0.0) {
+    CK(cudaStreamSynchronize(st));
+    return finish(0, true, 0.0);
+  }
+  const bool timed = h->opt.time_kernels != 0;
+  const int pl = balanced(h) ? kBalancedLaunches : 2 + ((h->coarse && h->n0 > 0) ? 1 : 0);
+  // u = b / beta, s = A^T u, t = M^{-1} s, alpha = (s.t)^{1/2}, v = t / alpha, q = s / alpha, w = v
+  double beta = std::sqrt(bb);
+  lsq::launch_axpby(m, 1.0 / beta, h->bv.p, 0.0, nullptr, h->lq_u.p, st);
+  lsq::launch_spmv_csc(csc(h), h->lq_u.p, h->lq_s.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, st);
+  precond(h, h->lq_s.p, h->lq_t.p, 0, true, false);
+  double alpha = std::sqrt(dev_sum(h, lsq::S_RZ));
+  CK(cudaMemsetAsync(h->lq_w.p, 0, sizeof(double) * n, st));
+  lsq::launch_lsqr_step(n, 1.0 / alpha, 0.0, -1.0, h->lq_t.p, h->lq_s.p, h->lq_v.p, h->lq_q.p, h->x.p, h->lq_w.p,
+                        st);  // v, q; w = v (x unchanged)
+  launches += 3 + pl + 1;
+  inf.local_launches += 1;
+  std::vector<double> al{alpha}, be{beta};
+  double phibar = beta, rhobar = alpha;
+  const double est0 = alpha * beta;
+  const int fixed = h->opt.fixed_iters;
+  const int maxit = fixed > 0 ? fixed : h->opt.maxit;
+  bool converged = false, checking = false, have_rel = false;
+  double rel = 1.0;
+  int it = 0;
+  while (it < maxit) {
+    if (timed) record_event(h->ev[0], st);
+    // beta u = A v - alpha u
+    lsq::launch_spmv_csr(csr(h), h->lq_v.p, h->q.p, h->lanes_csr, h->grid_csr, st);
+    lsq::launch_axpby(m, 1.0, h->q.p, -alpha, h->lq_u.p, h->lq_u.p, st);
+    lsq::launch_dot(m, h->lq_u.p, h->lq_u.p, site(h, lsq::S_TMP, 3), st);
+    beta = std::sqrt(dev_sum(h));
+    if (!(beta > 0.0) || !std::isfinite(beta)) {
+      if (beta == 0.0) { converged = true; break; }  // b lies in range(A V_k): x_k solves the problem
+      throw LsError(LS_ERR_NONFINITE, "LSQR breakdown (beta) at iteration " + std::to_string(it + 1));
+    }
+    lsq::launch_axpby(m, 1.0 / beta, h->lq_u.p, 0.0, nullptr, h->lq_u.p, st);
+    // alpha v = M^{-1} (A^T u - beta q)
+    lsq::launch_spmv_csc(csc(h), h->lq_u.p, h->lq_s.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, st);
+    if (timed) record_event(h->ev[1], st);
+    lsq::launch_axpby(n, 1.0, h->lq_s.p, -beta, h->lq_q.p, h->lq_s.p, st);
+    precond(h, h->lq_s.p, h->lq_t.p, 0, true, false, timed);
+    alpha = std::sqrt(dev_sum(h, lsq::S_RZ));
+    if (dev_sum(h, lsq::S_ERR) != 0.0)
+      throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up at iteration " +
+                                               std::to_string(it + 1));
+    if (!(alpha > 0.0) || !std::isfinite(alpha))
+      throw LsError(LS_ERR_NONFINITE, "LSQR breakdown (alpha) at iteration " + std::to_string(it + 1));
+    // plane rotation
+    const double rho = std::hypot(rhobar, beta);
+    const double c = rhobar / rho, sn = beta / rho;
+    const double theta = sn * alpha;
+    rhobar = -c * alpha;
+    const double phi = c * phibar;
+    phibar = sn * phibar;
+    lsq::launch_lsqr_step(n, 1.0 / alpha, phi / rho, theta / rho, h->lq_t.p, h->lq_s.p, h->lq_v.p, h->lq_q.p,
+                          h->x.p, h->lq_w.p, st);
+    if (timed) record_event(h->ev[5], st);
+    ++it;
+    launches += 6 + pl + 1;
+    inf.local_launches += 1;
+    al.push_back(alpha);
+    be.push_back(beta);
+    if (timed) {
+      CK(cudaStreamSynchronize(st));
+      float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
+      CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[1]));
+      CK(cudaEventElapsedTime(&tb, h->ev[2], h->ev[3]));
+      CK(cudaEventElapsedTime(&tc, h->ev[3], h->ev[4]));
+      CK(cudaEventElapsedTime(&td, h->ev[0], h->ev[5]));
+      inf.ms_spmv += ta; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
+    }
+    if (fixed > 0) continue;
+    if (!checking && phibar * alpha * std::fabs(c) <= 10.0 * rtol * est0) checking = true;
+    if (checking) {
+      rel = std::sqrt(true_residual(h, 0, &launches)) / gn;
+      have_rel = true;
+      if (rel <= rtol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  if (!converged || fixed > 0 || !have_rel) rel = std::sqrt(true_residual(h, 0, &launches)) / gn;
+  // kappa of M^{-1} A^T A from the bidiagonal: B_k^T B_k is the Lanczos matrix
+  const int k = (int)al.size() - 1;
+  if (k >= 1) {
+    std::vector<double> d(k), e(std::max(k - 1, 0));
+    for (int j = 0; j < k; ++j) {
+      d[j] = al[j] * al[j] + be[j + 1] * be[j + 1];
+      if (j + 1 < k) e[j] = al[j + 1] * be[j + 1];
+    }
+    const double lmax = tridiag_extreme(d, e, true), lmin = tridiag_extreme(d, e, false);
+    inf.kappa_lanczos = lmin > 0 ? lmax / lmin : 0.0;
+  }
+  return finish(it, converged, rel);
 }
 
 template <class F>
@@ -847,6 +985,10 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   if (h->opt.variant == 1) {
     h->bal_y.alloc(h->n); h->bal_t.alloc(h->n); h->bal_u.alloc(h->n); h->bal_v.alloc(h->n);
   }
+  if (h->opt.solver == 1) {
+    h->lq_u.alloc(h->m);
+    h->lq_v.alloc(h->n); h->lq_q.alloc(h->n); h->lq_s.alloc(h->n); h->lq_t.alloc(h->n); h->lq_w.alloc(h->n);
+  }
   h->parts.alloc(2 * (size_t)lsq::kMaxGrid);
   h->counters.alloc(8); h->counters.zero(st);
   h->scal.alloc(lsq::S_NSLOT); h->scal.zero(st);
@@ -883,6 +1025,7 @@ void ls_default_options(ls_options* o) {
   o->time_kernels = 0;
   o->equilibrate = 0;
   o->variant = 0;
+  o->solver = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -906,6 +1049,7 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.maxit < 1 && h->opt.fixed_iters < 1) throw LsError(LS_ERR_INVALID, "maxit must be positive");
     if (h->opt.nev_max < 0) throw LsError(LS_ERR_INVALID, "nev_max must be >= 0");
     if (h->opt.variant < 0 || h->opt.variant > 1) throw LsError(LS_ERR_INVALID, "variant must be 0 or 1");
+    if (h->opt.solver < 0 || h->opt.solver > 1) throw LsError(LS_ERR_INVALID, "solver must be 0 or 1");
     if (h->opt.variant == 1 && nprob > 1)
       throw LsError(LS_ERR_UNSUPPORTED, "the balanced variant is implemented for single-problem handles");
     if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
@@ -963,13 +1107,17 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
     if (!h || !b || !x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
     if (!(rtol > 0) && h->opt.fixed_iters <= 0) throw LsError(LS_ERR_INVALID, "rtol must be positive");
     CK(cudaSetDevice(h->dev));
-    if (nrhs > 1 || h->nprob > 1) return block_solve(h, b, nrhs, rtol, x, info);
+    if (nrhs > 1 || h->nprob > 1) {
+      if (h->opt.solver != 0)
+        throw LsError(LS_ERR_UNSUPPORTED, "the LSQR outer solver takes one right-hand side of a single problem");
+      return block_solve(h, b, nrhs, rtol, x, info);
+    }
     ls_status last = LS_OK;
     for (int k = 0; k < nrhs; ++k) {
       // b' = P b for the row-reordered device matrix
       CK(cudaMemcpyAsync(h->q.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, h->st));
       lsq::launch_gather(h->m, h->perm.p, h->q.p, h->bv.p, h->st);
-      ls_status s = solve_core(h, 0, rtol, info);
+      ls_status s = h->opt.solver == 1 ? lsqr_core(h, rtol, info) : solve_core(h, 0, rtol, info);
       CK(cudaMemcpyAsync(x + (int64_t)k * h->n, h->x.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
       CK(cudaStreamSynchronize(h->st));
       if (s != LS_OK) last = s;

@@ -68,7 +68,7 @@ void ensure_buffers(ls_handle* h, int R) {
 void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool flex, bool timed) {
   BlockState& B = h->blk;
   cudaStream_t st = h->st;
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[2], st);
   lsq::BLocalArgs a{};
   a.N = h->N; a.order = B.order.p; a.qctr = B.qctr.p;
   a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
@@ -85,7 +85,7 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   } else {
     lsq::launch_b_local(h->prec, a, B.local_grid, st);
   }
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[3], st);
   const bool coarse = h->coarse && h->n0 > 0;
   const bool zt = coarse && B.ZT.p != nullptr;
   if (coarse) {
@@ -97,7 +97,7 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
     lsq::launch_b_coarse(B.nct, R, B.ct_prob.p, B.ct_row.p, cb, B.n0q.p, h->Xinv.p, B.R0.p, B.Y0.p,
                          zt ? B.Y0f.p : nullptr, st);
   }
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[4], st);
   lsq::BScatterArgs s{};
   s.R = R;
   s.Rp = 1;
@@ -120,10 +120,10 @@ void iteration_block(ls_handle* h, int R, bool flex) {
   const lsq::BScal sc = scal(h);
   const lsq::BChunks ch = chunks(h);
   double* part2 = B.parts.p + (size_t)B.nchunks * 32;
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[0], st);
   lsq::launch_b_spmm_csr(csr(h), B.P.p, B.Q.p, R, st);
   lsq::launch_b_spmm_csc(ch, csc(h), B.Q.p, B.W.p, R, B.P.p, B.parts.p, st);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[1], st);
   lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinAlpha, 0, st);
   lsq::launch_b_update(ch, R, sc.alpha, B.P.p, B.W.p, B.X.p, B.Rv.p, flex ? B.Rold.p : nullptr, B.parts.p, st);
   CK(cudaMemsetAsync(B.stat.p, 0, sizeof(int), st));
@@ -132,7 +132,7 @@ void iteration_block(ls_handle* h, int R, bool flex) {
   lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, flex ? part2 : nullptr, R, sc, lsq::kFinBeta, flex ? 1 : 0,
                        st);
   lsq::launch_b_pupdate(ch, R, sc.beta, B.Z.p, B.P.p, 0, st);
-  if (timed) CK(cudaEventRecordWithFlags(h->ev[5], st, cudaEventRecordExternal));
+  if (timed) record_event(h->ev[5], st);
   CK(cudaMemcpyAsync(B.pin, B.stat.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(B.pin + 2, h->scal.p + lsq::S_ERR, sizeof(double), cudaMemcpyDeviceToHost, st));
 }

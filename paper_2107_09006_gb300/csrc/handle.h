@@ -67,6 +67,15 @@ inline double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Records a timing event on st: as an external node while st is being captured into a
+// graph (so the replay records it), as a plain record otherwise.
+inline void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else CK(cudaEventRecord(ev, st));
+}
+
 inline void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw LsError(LS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -153,6 +162,7 @@ struct ls_handle {
 
   DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
   DevBuf<double> bal_y, bal_t, bal_u, bal_v;  // work vectors of the balanced variant
+  DevBuf<double> lq_u, lq_v, lq_q, lq_s, lq_t, lq_w;  // LSQR: u (m), v, M v, s, M^{-1} s, w
   DevBuf<double> parts, scal, ahist, bhist;
   DevBuf<unsigned> counters;  // ticket counters of the fused reductions
   DevBuf<int> ctr;

@@ -323,6 +323,22 @@ __global__ void __launch_bounds__(kThreads) k_combine3(int64_t n, const double* 
   if (ds.parts) finish_dots(d1, d2, r_old != nullptr, ds);
 }
 
+// The vector updates of one preconditioned LSQR step: v = t / alpha, q = s / alpha
+// (q = M v), x += c1 w, w = v - c2 w.
+__global__ void __launch_bounds__(kThreads) k_lsqr_step(int64_t n, double inv_alpha, double c1, double c2,
+                                                        const double* __restrict__ t, const double* __restrict__ s,
+                                                        double* __restrict__ v, double* __restrict__ q,
+                                                        double* __restrict__ x, double* __restrict__ w) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double vk = t[k] * inv_alpha;
+    v[k] = vk;
+    q[k] = s[k] * inv_alpha;
+    const double wk = w[k];
+    x[k] += c1 * wk;
+    w[k] = vk - c2 * wk;
+  }
+}
+
 // y0 = X r0 for the dense n0 x n0 coarse inverse (one warp per row).
 __global__ void __launch_bounds__(kThreads) k_gemv(int64_t n0, const double* __restrict__ X,
                                                    const double* __restrict__ r0, double* __restrict__ y0) {
@@ -449,6 +465,11 @@ void launch_gather64(int64_t n, const int64_t* idx, const double* src, double* d
 void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, const double* src, double* dst,
                         int accumulate, cudaStream_t st) {
   k_scatter_idx<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, idx32, idx64, src, dst, accumulate);
+}
+
+void launch_lsqr_step(int64_t n, double inv_alpha, double c1, double c2, const double* t, const double* s, double* v,
+                      double* q, double* x, double* w, cudaStream_t st) {
+  k_lsqr_step<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, inv_alpha, c1, c2, t, s, v, q, x, w);
 }
 
 void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,

@@ -69,6 +69,10 @@ struct ScatterArgs {
   int add_coarse_only;  // 1: z = coarse term only; 2: z = local sum only
 };
 void launch_scatter(const ScatterArgs& a, cudaStream_t st);
+// One preconditioned LSQR step's vector updates: v = t / alpha, q = s / alpha, x += c1 w,
+// w = v - c2 w.
+void launch_lsqr_step(int64_t n, double inv_alpha, double c1, double c2, const double* t, const double* s, double* v,
+                      double* q, double* x, double* w, cudaStream_t st);
 // r0 = R_0 v (coarse restriction alone, FP64)
 void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,
                      const double* Z, const double* v, double* r0, cudaStream_t st);
