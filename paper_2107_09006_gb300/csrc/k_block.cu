@@ -769,9 +769,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
     };
     if (tid == 0)
       while (pnext < 2 * ntile && issued < q + S) issue();
-    auto wait_tile = [&]() -> const float* {
-      const int stage = (int)(q % S);
-      const uint32_t parity = (q / S) & 1u;
+    // tile q + off of the sequence (off = 0, 1; both are in flight: S >= 2)
+    auto wait_tile = [&](uint32_t off) -> const float* {
+      const int stage = (int)((q + off) % S);
+      const uint32_t parity = ((q + off) / S) & 1u;
       if (!bar_try_wait(&bars[stage], parity)) {
         const long long c0 = clock64();
         bool ok = false;
@@ -783,11 +784,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
     };
     // (on a give-up q keeps pointing at the tile that was waited for, so the final
     // drain covers it)
-    auto release = [&]() -> bool {
+    auto release = [&](uint32_t used) -> bool {
       __syncthreads();
       if (sh[1]) return false;
-      ++q;
-      if (tid == 0 && pnext < 2 * ntile) issue();
+      q += used;
+      if (tid == 0)
+        while (pnext < 2 * ntile && issued < q + S) issue();
       return true;
     };
     bool ok = true;
@@ -811,14 +813,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       }
       if (b + 1 < nbk) fetch_rhs(b + 1);
       __syncthreads();
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int t = tf[b]; t < b && ok; ++t) {
-        const float* T = wait_tile();
+      // panel tiles two at a time (independent products, one barrier per pair)
+      float c[4] = {0.f, 0.f, 0.f, 0.f}, c2[4] = {0.f, 0.f, 0.f, 0.f};
+      int t = tf[b];
+      for (; t + 1 < b && ok; t += 2) {
+        const float* T1 = wait_tile(0);
+        const float* T2 = wait_tile(1);
+        tile_mma<false>(T1, vring + (size_t)(t % RING) * kT * kT, c, mb, nb, g, t4);
+        tile_mma<false>(T2, vring + (size_t)((t + 1) % RING) * kT * kT, c2, mb, nb, g, t4);
+        ok = release(2);
+      }
+      if (ok && t < b) {
+        const float* T = wait_tile(0);
         tile_mma<false>(T, vring + (size_t)(t % RING) * kT * kT, c, mb, nb, g, t4);
-        ok = release();
+        ok = release(1);
       }
       if (!ok) break;
-      const float* D = wait_tile();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] += c2[u];
+      const float* D = wait_tile(0);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float2* p = frag_ptr(tin, mb, nb, g, t4, h);
@@ -838,14 +851,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) *frag_ptr(sp, mb, nb, g, t4, h) = make_float2(y[2 * h], y[2 * h + 1]);
       }
-      ok = release();
+      ok = release(1);
     }
     // backward sweep
     for (int b = nbk - 1; b >= 0 && ok; --b) {
       // the forward values of tile b - RING, which takes slot b % RING after this step
       float4 refill = make_float4(0.f, 0.f, 0.f, 0.f);
       if (b - RING >= 0) refill = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT)[tid];
-      const float* D = wait_tile();
+      const float* D = wait_tile(0);
       float x[4] = {0.f, 0.f, 0.f, 0.f};
       tile_mma<true>(D, vring + (size_t)(b % RING) * kT * kT, x, mb, nb, g, t4);
 #pragma unroll
@@ -859,21 +872,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
           if (k + 1 < R) a.Y[(o0 + l) * R + k + 1] = (double)x[2 * h + 1] * sc;
         }
       }
-      ok = release();
-      for (int t = b - 1; t >= tf[b] && ok; --t) {
-        const float* T = wait_tile();
-        float s[4] = {0.f, 0.f, 0.f, 0.f};
-        tile_mma<true>(T, tin, s, mb, nb, g, t4);
-        float* vt = vring + (size_t)(t % RING) * kT * kT;
+      ok = release(1);
+      // window updates v_t -= L_bt^T x_b, two tiles (two different slots) per barrier
+      auto update = [&](const float* T, int tt) {
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+        tile_mma<true>(T, tin, s4, mb, nb, g, t4);
+        float* vt = vring + (size_t)(tt % RING) * kT * kT;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float2* p = frag_ptr(vt, mb, nb, g, t4, h);
           float2 v = *p;
-          v.x -= s[2 * h];
-          v.y -= s[2 * h + 1];
+          v.x -= s4[2 * h];
+          v.y -= s4[2 * h + 1];
           *p = v;
         }
-        ok = release();
+      };
+      int t = b - 1;
+      for (; t - 1 >= tf[b] && ok; t -= 2) {
+        const float* T1 = wait_tile(0);
+        const float* T2 = wait_tile(1);
+        update(T1, t);
+        update(T2, t - 1);
+        ok = release(2);
+      }
+      if (ok && t >= tf[b]) {
+        update(wait_tile(0), t);
+        ok = release(1);
       }
       if (ok && b - RING >= 0) {
         reinterpret_cast<float4*>(vring + (size_t)(b % RING) * kT * kT)[tid] = refill;
