@@ -673,10 +673,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
 // output rows [16 (w / 4), +16) and right-hand sides [8 (w % 4), +8).  The solution
 // operand is split into a TF32 head and a TF32 tail (two MMAs), which keeps it at
 // about FP32 accuracy; the factor is TF32 (stored pre-rounded).  Factor and solution
-// tiles are row-major with the swizzle (r, c) -> 32 r + ((c + 8 (r % 4) + 4 ((r / 4) % 2)) % 32):
-// the fragments of T, of T^T and of the solution tile then all hit 32 distinct banks.
+// tiles are row-major with the swizzle (r, c) -> 32 r + (c xor s(r)), s(r) = 8 (r % 4) +
+// 4 ((r / 4) % 2): the fragments of T, of T^T and of the solution tile then all hit 32
+// distinct banks, and each fragment address is a per-thread offset (TcOff) plus a
+// multiple of 256.
 
-__device__ __forceinline__ int swz(int r, int c) { return r * kT + ((c + 8 * (r & 3) + 4 * ((r >> 2) & 1)) & 31); }
+__device__ __forceinline__ int swz(int r, int c) { return r * kT + (c ^ (8 * (r & 3) + 4 * ((r >> 2) & 1))); }
+
+// Fragment offsets of one thread (lane = 4 g + t of warp (mb, nb)):
+//   a[ks][j]  T(16 mb + g, 8 ks + t + 4 j)                 (+256: row + 8)
+//   t[h][j]   T(8 ks + t + 4 j, 16 mb + g + 8 h) - 256 ks
+//   b[j]      V(8 ks + t + 4 j, 8 nb + g) - 256 ks
+//   o[h]      output pair (16 mb + g + 8 h, 8 nb + 2 t + {0, 1})
+struct TcOff {
+  int a[4][2], t[2][2], b[2], o[2];
+};
+
+__device__ __forceinline__ TcOff tc_offsets(int mb, int nb, int g, int t) {
+  TcOff f;
+  const int gb = (g >> 2) & 1, g3 = g & 3, r0 = 16 * mb + g;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) f.a[ks][j] = r0 * 32 + t + 8 * (ks ^ g3) + 4 * (j ^ gb);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) f.t[h][j] = 32 * t + 128 * j + 8 * ((2 * mb + h) ^ t) + 4 * (gb ^ j) + g3;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) f.b[j] = 32 * t + 128 * j + 8 * (nb ^ t) + 4 * (gb ^ j) + g3;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) f.o[h] = (r0 + 8 * h) * 32 + 8 * (nb ^ g3) + ((2 * t) ^ (4 * gb));
+  return f;
+}
 
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
   uint32_t y;
@@ -694,20 +723,23 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32
 // c += op(T) V on the warp's 16 x 8 output block; op(T) = T or T^T.  The head and
 // tail products go to two accumulators (two independent MMA chains), summed at the end.
 template <bool TRANS>
-__device__ __forceinline__ void tile_mma(const float* T, const float* V, float c[4], int mb, int nb, int g, int t) {
+__device__ __forceinline__ void tile_mma(const float* T, const float* V, float c[4], const TcOff& f) {
   float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int ks = 0; ks < 4; ++ks) {
-    const int r0 = mb * 16 + g, k0 = ks * 8 + t;
     uint32_t a[4];
     if (!TRANS) {
-      a[0] = __float_as_uint(T[swz(r0, k0)]);     a[1] = __float_as_uint(T[swz(r0 + 8, k0)]);
-      a[2] = __float_as_uint(T[swz(r0, k0 + 4)]); a[3] = __float_as_uint(T[swz(r0 + 8, k0 + 4)]);
+      a[0] = __float_as_uint(T[f.a[ks][0]]);
+      a[1] = __float_as_uint(T[f.a[ks][0] + 256]);
+      a[2] = __float_as_uint(T[f.a[ks][1]]);
+      a[3] = __float_as_uint(T[f.a[ks][1] + 256]);
     } else {
-      a[0] = __float_as_uint(T[swz(k0, r0)]);     a[1] = __float_as_uint(T[swz(k0, r0 + 8)]);
-      a[2] = __float_as_uint(T[swz(k0 + 4, r0)]); a[3] = __float_as_uint(T[swz(k0 + 4, r0 + 8)]);
+      a[0] = __float_as_uint(T[256 * ks + f.t[0][0]]);
+      a[1] = __float_as_uint(T[256 * ks + f.t[1][0]]);
+      a[2] = __float_as_uint(T[256 * ks + f.t[0][1]]);
+      a[3] = __float_as_uint(T[256 * ks + f.t[1][1]]);
     }
-    const float v0 = V[swz(k0, nb * 8 + g)], v1 = V[swz(k0 + 4, nb * 8 + g)];
+    const float v0 = V[256 * ks + f.b[0]], v1 = V[256 * ks + f.b[1]];
     const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
     const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
     mma_tf32(c, a, h0, h1);
@@ -718,8 +750,8 @@ __device__ __forceinline__ void tile_mma(const float* T, const float* V, float c
 }
 
 // The warp's accumulator elements: (row, col) of c[2 h + j] = (16 mb + g + 8 h, 8 nb + 2 t + j).
-__device__ __forceinline__ float2* frag_ptr(float* tile, int mb, int nb, int g, int t, int h) {
-  return reinterpret_cast<float2*>(tile + swz(mb * 16 + g + 8 * h, nb * 8 + 2 * t));
+__device__ __forceinline__ float2* frag_ptr(float* tile, const TcOff& f, int h) {
+  return reinterpret_cast<float2*>(tile + f.o[h]);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
@@ -732,6 +764,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
   int* sh = reinterpret_cast<int*>(bars + S);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int mb = w >> 2, nb = w & 3, g = lane >> 2, t4 = lane & 3;
+  const TcOff off = tc_offsets(mb, nb, g, t4);
   const int R = a.R, RING = a.ring;
   const float* fac = reinterpret_cast<const float*>(a.fac);
   float* spill = reinterpret_cast<float*>(a.Vg);
@@ -819,13 +852,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       for (; t + 1 < b && ok; t += 2) {
         const float* T1 = wait_tile(0);
         const float* T2 = wait_tile(1);
-        tile_mma<false>(T1, vring + (size_t)(t % RING) * kT * kT, c, mb, nb, g, t4);
-        tile_mma<false>(T2, vring + (size_t)((t + 1) % RING) * kT * kT, c2, mb, nb, g, t4);
+        tile_mma<false>(T1, vring + (size_t)(t % RING) * kT * kT, c, off);
+        tile_mma<false>(T2, vring + (size_t)((t + 1) % RING) * kT * kT, c2, off);
         ok = release(2);
       }
       if (ok && t < b) {
         const float* T = wait_tile(0);
-        tile_mma<false>(T, vring + (size_t)(t % RING) * kT * kT, c, mb, nb, g, t4);
+        tile_mma<false>(T, vring + (size_t)(t % RING) * kT * kT, c, off);
         ok = release(1);
       }
       if (!ok) break;
@@ -834,7 +867,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       const float* D = wait_tile(0);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        float2* p = frag_ptr(tin, mb, nb, g, t4, h);
+        float2* p = frag_ptr(tin, off, h);
         float2 v = *p;
         v.x -= c[2 * h];
         v.y -= c[2 * h + 1];
@@ -842,14 +875,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       }
       __syncthreads();
       float y[4] = {0.f, 0.f, 0.f, 0.f};
-      tile_mma<false>(D, tin, y, mb, nb, g, t4);
+      tile_mma<false>(D, tin, y, off);
       float* vb = vring + (size_t)(b % RING) * kT * kT;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) *frag_ptr(vb, mb, nb, g, t4, h) = make_float2(y[2 * h], y[2 * h + 1]);
+      for (int h = 0; h < 2; ++h) *frag_ptr(vb, off, h) = make_float2(y[2 * h], y[2 * h + 1]);
       if (b < nbk - RING) {
         float* sp = spill + (size_t)(b0 + b) * kT * kT;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) *frag_ptr(sp, mb, nb, g, t4, h) = make_float2(y[2 * h], y[2 * h + 1]);
+        for (int h = 0; h < 2; ++h) *frag_ptr(sp, off, h) = make_float2(y[2 * h], y[2 * h + 1]);
       }
       ok = release(1);
     }
@@ -860,10 +893,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       if (b - RING >= 0) refill = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT)[tid];
       const float* D = wait_tile(0);
       float x[4] = {0.f, 0.f, 0.f, 0.f};
-      tile_mma<true>(D, vring + (size_t)(b % RING) * kT * kT, x, mb, nb, g, t4);
+      tile_mma<true>(D, vring + (size_t)(b % RING) * kT * kT, x, off);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        *frag_ptr(tin, mb, nb, g, t4, h) = make_float2(x[2 * h], x[2 * h + 1]);
+        *frag_ptr(tin, off, h) = make_float2(x[2 * h], x[2 * h + 1]);
         const int l = b * kT + mb * 16 + g + 8 * h;
         const int k = nb * 8 + 2 * t4;
         if (l < ni) {
@@ -876,11 +909,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       // window updates v_t -= L_bt^T x_b, two tiles (two different slots) per barrier
       auto update = [&](const float* T, int tt) {
         float s4[4] = {0.f, 0.f, 0.f, 0.f};
-        tile_mma<true>(T, tin, s4, mb, nb, g, t4);
+        tile_mma<true>(T, tin, s4, off);
         float* vt = vring + (size_t)(tt % RING) * kT * kT;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float2* p = frag_ptr(vt, mb, nb, g, t4, h);
+          float2* p = frag_ptr(vt, off, h);
           float2 v = *p;
           v.x -= s4[2 * h];
           v.y -= s4[2 * h + 1];
