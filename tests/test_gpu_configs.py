@@ -7,6 +7,8 @@
   differentiates one smooth map and its error is the truncation error of the
   difference plus rounding, not the solver tolerance.
 * The autograd function LSSolve against the oracle's dense gradient (n = 1024).
+* The mixed forms' gradients (FP32 / BF16 local factors in the forward and adjoint
+  solves) against the FP64 form's on the n = 262,144 workload.
 * Precision (column-scaled A, u_j ~ U(-3, 3), 96x96 grid, 9 subdomains): with column
   equilibration the FP64, FP32 and BF16 factor forms reach the true residual tolerance
   and are as accurate as the FP64 oracle at that tolerance; the equilibrated
@@ -160,3 +162,23 @@ def test_paper_shift_on_scaled_columns(scaled):
     print(f"paper shift f32 rtol 1e-8: {info['iters']} iterations, relative error {err:.2e} "
           f"(oracle: {st['iters']} iterations, {err_o:.2e})")
     S.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_mixed_form_gradient_matches_fp64(prec):
+    """Differentiation in the mixed forms (n = 262,144, 64 subdomains): the forward solve
+    and the adjoint solve run flexible PCG with FP32 / BF16 local factors to 1e-12; both
+    gradients (b and the values of A) agree with the FP64 form's to 1e-8 relative, the
+    level a 1e-12 solve tolerance allows through kappa(C)."""
+    P = config_diff()
+    xs = torch.as_tensor(P.xstar, device="cuda")
+    grads = {}
+    for form in ("f64", prec):
+        S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=32, factor_prec=form)
+        x, info = S.solve(P.b, rtol=1e-12)
+        assert info["relres_true"] <= 1e-12
+        gb, gv, _ = S.backward(P.b, x, 2.0 * (x - xs), rtol=1e-12)
+        grads[form] = (gb.cpu().numpy(), gv.cpu().numpy())
+        S.close()
+    for a, b in zip(grads[prec], grads["f64"]):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
