@@ -56,11 +56,13 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-side", type=int, default=256, help="grid side of the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--mode", default="solve", choices=["solve", "nsweep", "precision", "batch", "tausweep"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "nsweep", "precision", "batch", "tausweep", "diff"],
                     help="solve: the timed benchmark line; nsweep: iterations/setup vs subdomain count "
                          "(blocks 128/64/32); precision: errors of every form on the column-scaled workload; "
                          "batch: 64 independent problems x 32 right-hand sides in shared launches; "
-                         "tausweep: iterations and n0 against the threshold tau")
+                         "tausweep: iterations and n0 against the threshold tau; "
+                         "diff: forward + adjoint solves on the n = 262,144 differentiation workload")
     ap.add_argument("--zero-sum", action="store_true",
                     help="nsweep/tausweep on the zero-sum variant of the grid workload (random rows centred to "
                          "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
@@ -527,6 +529,56 @@ def run_tausweep(args):
                       f"rtol {args.rtol:g}, nev_max 64", "rows": rows}), flush=True)
 
 
+def run_diff(args):
+    """Differentiation workload (512 x 512 grid, n = 262,144, 64 subdomains, x* drawn):
+    loss ||x(A, b) - x*||^2; one step is the forward solve plus the adjoint solve that
+    gives the gradients with respect to b and the stored values of A (LSSolve's forward
+    and backward), each to 1e-10, in the FP64 and the mixed forms; the mixed forms'
+    gradients are compared with the FP64 form's."""
+    torch, dev = _device_setup()
+    import numpy as np
+    from paper_2107_09006_gb300 import Solver
+    from workloads import config_diff
+    P = config_diff()
+    stream = torch.cuda.current_stream(dev)
+    b = torch.as_tensor(P.b, device=dev)
+    xs = torch.as_tensor(P.xstar, device=dev)
+    rows, ref = [], None
+    for form in ("f64", "f32", "bf16"):
+        S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
+                   nev_max=args.nev, factor_prec=form)
+
+        def step():
+            x, fi = S.solve(b, rtol=1e-10)
+            gb, gv, bi = S.backward(b, x, 2.0 * (x - xs), rtol=1e-10)
+            return x, gb, gv, fi, bi
+
+        for _ in range(max(args.warmup, 1)):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            x, gb, gv, fi, bi = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        g = (gb.cpu().numpy(), gv.cpu().numpy())
+        row = {"form": form, "s_per_step": e0.elapsed_time(e1) / 1000.0 / args.steps,
+               "forward_iterations": fi["iters"], "adjoint_iterations": bi["iters"],
+               "adjoint_relres_true": bi["relres_true"]}
+        if form == "f64":
+            ref = g
+        else:
+            row["grad_b_rel_diff_vs_f64"] = float(np.linalg.norm(g[0] - ref[0]) / np.linalg.norm(ref[0]))
+            row["grad_vals_rel_diff_vs_f64"] = float(np.linalg.norm(g[1] - ref[1]) / np.linalg.norm(ref[1]))
+        log(f"[diff] {json.dumps(row)}")
+        rows.append(row)
+        S.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"report": "diff", "workload": f"{P.name}: n={P.n}, m={P.m}, nnz={P.nnz}, 64 subdomains, "
+                      f"nev_max {args.nev}, rtol 1e-10 forward and adjoint", "rows": rows}), flush=True)
+
+
 def run_batch(args):
     """Batched workload: 64 independent problems (n log-uniform in [16384, 262144],
     square grids, 4n rows of 6 nonzeros within radius 2 plus 1e-2 I, uneven bisection
@@ -619,5 +671,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.mode == "tausweep":
         run_tausweep(a)
+    elif a.mode == "diff":
+        run_diff(a)
     else:
         run_ours(a)
