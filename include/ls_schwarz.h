@@ -187,7 +187,9 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
  *   grad_vals[k] = rho_r lambda_c - (A lambda)_r x_c    for CSR entry k = (r, c),
  *                  rho = b - A x                        (summed over right-hand sides)
  * b, x, grad_x are the forward inputs/outputs (column-major, host or device);
- * grad_b or grad_vals may be NULL to skip them.  Batched handles: LS_ERR_UNSUPPORTED. */
+ * grad_b or grad_vals may be NULL to skip them.  On a batched handle the adjoint solves of
+ * all (problem, right-hand side) pairs run together on the block path (nrhs <= 32), each
+ * to its own test relative to its ||grad_x||; grad_vals is summed over the pairs. */
 ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x,
                       int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info);
 

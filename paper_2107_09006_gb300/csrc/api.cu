@@ -1130,7 +1130,10 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
                       double* grad_b, double* grad_vals, ls_info* info) {
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || !grad_x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
-    if (h->nprob > 1) throw LsError(LS_ERR_UNSUPPORTED, "ls_backward on a batched handle");
+    if (h->nprob > 1) {
+      CK(cudaSetDevice(h->dev));
+      return block_backward(h, b, x, grad_x, nrhs, rtol, grad_b, grad_vals, info);
+    }
     CK(cudaSetDevice(h->dev));
     cudaStream_t st = h->st;
     ls_status last = LS_OK;

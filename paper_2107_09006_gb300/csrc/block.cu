@@ -147,14 +147,20 @@ std::vector<T> fetch(const T* p, size_t n, cudaStream_t st) {
   return v;
 }
 
-// tt = ||A^T (B - A X)||^2 per pair (W receives the residual vectors).
-std::vector<double> true_residual_block(ls_handle* h, int R, int* launches) {
+// tt per pair, W receiving the residual vectors: mode 0 ||A^T (B - A X)||^2 (b given),
+// mode 1 ||G - A^T (A X)||^2 (the normal-equations right-hand side G given).
+std::vector<double> true_residual_block(ls_handle* h, int R, int mode, int* launches) {
   BlockState& B = h->blk;
   cudaStream_t st = h->st;
   const lsq::BScal sc = scal(h);
   lsq::launch_b_spmm_csr(csr(h), B.X.p, B.Q.p, R, st);
-  lsq::launch_b_sub((int64_t)h->m * R, B.B.p, B.Q.p, st);
-  lsq::launch_b_spmm_csc(chunks(h), csc(h), B.Q.p, B.W.p, R, nullptr, B.parts.p, st);
+  if (mode == 0) {
+    lsq::launch_b_sub((int64_t)h->m * R, B.B.p, B.Q.p, st);
+    lsq::launch_b_spmm_csc(chunks(h), csc(h), B.Q.p, B.W.p, R, nullptr, B.parts.p, st);
+  } else {
+    lsq::launch_b_spmm_csc(chunks(h), csc(h), B.Q.p, B.W.p, R, nullptr, nullptr, st);
+    lsq::launch_b_resid(chunks(h), R, B.G.p, B.W.p, B.parts.p, st);
+  }
   lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinTT, 0, st);
   *launches += 4;
   return fetch(sc.tt, (size_t)h->nprob * R, st);
@@ -237,36 +243,36 @@ void block_plan(ls_handle* h) {
   check_launch("block plan");
 }
 
-ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double* x, ls_info* info) {
-  BlockState& B = h->blk;
-  cudaStream_t st = h->st;
+namespace {
+
+void check_block(const ls_handle* h, int R) {
   if (R < 1 || R > 32) throw LsError(LS_ERR_UNSUPPORTED, "the multi right-hand-side path takes 1 to 32 right-hand sides");
   if (h->opt.variant != 0)
     throw LsError(LS_ERR_UNSUPPORTED, "the multi right-hand-side path applies the additive two-level operator");
-  if (!B.local_ok)
-    throw LsError(LS_ERR_UNSUPPORTED, "the widest local factor block row (" + std::to_string(B.ring) +
+  if (!h->blk.local_ok)
+    throw LsError(LS_ERR_UNSUPPORTED, "the widest local factor block row (" + std::to_string(h->blk.ring) +
                                           " tiles) does not fit the multi right-hand-side local solve");
-  const double t0 = now_s();
+}
+
+// the caller's column-major array (host or device, rows x R) as a device pointer
+// (host data goes through the staging buffer Bu)
+const double* device_view(ls_handle* h, const double* p, int64_t rows, int R) {
+  if (is_device_ptr(p)) return p;
+  CK(cudaMemcpyAsync(h->blk.Bu.p, p, sizeof(double) * rows * R, cudaMemcpyHostToDevice, h->st));
+  return h->blk.Bu.p;
+}
+
+// Block PCG from x = 0 once Rv holds the normal-equations right-hand side of every pair
+// and gg its squared norms; mode 0: b in B (true residual A^T (b - A x)), mode 1: G
+// given (true residual G - A^T A x).  Result in X.  Returns whether all pairs passed.
+bool block_core(ls_handle* h, int R, double rtol, int mode, const std::vector<double>& gg, ls_info& inf,
+                int& launches) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
   const bool flex = h->prec != LS_PREC_F64;
   const int NP = h->nprob * R;
-  ensure_buffers(h, R);
-  ls_info inf{};
-  inf.bad_subdomain = -1;
-  int launches = 0;
   const lsq::BScal sc = scal(h);
   const lsq::BChunks ch = chunks(h);
-  // B = P b (interleaved), R = G = A^T B, gg = ||G||^2
-  const double* bsrc = b;
-  if (!is_device_ptr(b)) {
-    CK(cudaMemcpyAsync(B.Bu.p, b, sizeof(double) * h->m * R, cudaMemcpyHostToDevice, st));
-    bsrc = B.Bu.p;
-  }
-  lsq::launch_b_load_rows(h->m, R, h->perm.p, bsrc, B.B.p, st);
-  lsq::launch_b_spmm_csc(ch, csc(h), B.B.p, B.Rv.p, R, nullptr, B.parts.p, st);
-  CK(cudaMemsetAsync(B.act.p, 0, sizeof(int) * NP, st));
-  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinGG, 0, st);
-  launches += 3;
-  std::vector<double> gg = fetch(sc.gg, NP, st);
   const int fixed = h->opt.fixed_iters;
   std::vector<double> thr2(NP);
   std::vector<int> act(NP);
@@ -345,7 +351,7 @@ ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double*
                                           std::to_string(it));
     if (fixed > 0) continue;
     if (B.pin[0] == 0) {
-      tt = true_residual_block(h, R, &launches);
+      tt = true_residual_block(h, R, mode, &launches);
       int fail = 0;
       for (int i = 0; i < NP; ++i) {
         act[i] = (gg[i] > 0.0 && tt[i] > thr2[i]) ? 1 : 0;
@@ -361,15 +367,7 @@ ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double*
       restart();
     }
   }
-  if (tt.empty() || !converged) tt = true_residual_block(h, R, &launches);
-  // x (caller's column-major layout)
-  if (is_device_ptr(x)) {
-    lsq::launch_b_store_cols(h->n, R, B.X.p, x, st);
-  } else {
-    lsq::launch_b_store_cols(h->n, R, B.X.p, B.Bu.p, st);
-    CK(cudaMemcpyAsync(x, B.Bu.p, sizeof(double) * h->n * R, cudaMemcpyDeviceToHost, st));
-  }
-  launches += 1;
+  if (tt.empty() || !converged) tt = true_residual_block(h, R, mode, &launches);
   std::vector<int> its = fetch(sc.its, NP, st);
   std::vector<double> rr = fetch(sc.rr, NP, st);
   check_launch("block solve");
@@ -390,13 +388,101 @@ ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double*
   inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.eig_steps_max = h->sinfo.eig_steps_max;
-  inf.launches = launches;
   inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  return converged || fixed > 0;
+}
+
+}  // namespace
+
+ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double* x, ls_info* info) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  check_block(h, R);
+  const double t0 = now_s();
+  ensure_buffers(h, R);
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
+  const lsq::BScal sc = scal(h);
+  // B = P b (interleaved), R = A^T B, gg = ||A^T B||^2
+  lsq::launch_b_load_rows(h->m, R, h->perm.p, device_view(h, b, h->m, R), B.B.p, st);
+  lsq::launch_b_spmm_csc(chunks(h), csc(h), B.B.p, B.Rv.p, R, nullptr, B.parts.p, st);
+  CK(cudaMemsetAsync(B.act.p, 0, sizeof(int) * h->nprob * R, st));
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinGG, 0, st);
+  launches += 3;
+  const std::vector<double> gg = fetch(sc.gg, (size_t)h->nprob * R, st);
+  const bool ok = block_core(h, R, rtol, 0, gg, inf, launches);
+  // x (caller's column-major layout)
+  if (is_device_ptr(x)) {
+    lsq::launch_b_store_cols(h->n, R, B.X.p, x, st);
+  } else {
+    lsq::launch_b_store_cols(h->n, R, B.X.p, B.Bu.p, st);
+    CK(cudaMemcpyAsync(x, B.Bu.p, sizeof(double) * h->n * R, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  launches += 1;
+  inf.launches = launches;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
-  if (!converged && fixed <= 0)
+  if (!ok)
     throw LsError(LS_ERR_NOT_CONVERGED, "maximum number of iterations reached, worst true relative residual " +
-                                            std::to_string(worst));
+                                            std::to_string(inf.relres_true));
+  return LS_OK;
+}
+
+ls_status block_backward(ls_handle* h, const double* b, const double* x, const double* grad_x, int R, double rtol,
+                         double* grad_b, double* grad_vals, ls_info* info) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  check_block(h, R);
+  const double t0 = now_s();
+  ensure_buffers(h, R);
+  B.G.alloc((size_t)h->n * R);
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
+  const lsq::BScal sc = scal(h);
+  // lambda = C^{-1} grad_x for every pair: G = grad_x (interleaved), R = G, gg = ||G||^2
+  lsq::launch_b_load_cols(h->n, R, device_view(h, grad_x, h->n, R), B.G.p, st);
+  CK(cudaMemsetAsync(B.Rv.p, 0, sizeof(double) * h->n * R, st));
+  lsq::launch_b_resid(chunks(h), R, B.G.p, B.Rv.p, B.parts.p, st);
+  CK(cudaMemsetAsync(B.act.p, 0, sizeof(int) * h->nprob * R, st));
+  lsq::launch_b_finish(h->nprob, B.pc_off.p, B.parts.p, nullptr, R, sc, lsq::kFinGG, 0, st);
+  launches += 3;
+  const std::vector<double> gg = fetch(sc.gg, (size_t)h->nprob * R, st);
+  const bool ok = block_core(h, R, rtol, 1, gg, inf, launches);  // lambda in X
+  // A lambda (rows of the reordered matrix); grad_b = P^T A lambda
+  lsq::launch_b_spmm_csr(csr(h), B.X.p, B.Q.p, R, st);
+  if (grad_b) {
+    if (is_device_ptr(grad_b)) {
+      lsq::launch_b_store_rows(h->m, R, h->perm.p, B.Q.p, grad_b, st);
+    } else {
+      lsq::launch_b_store_rows(h->m, R, h->perm.p, B.Q.p, B.Bu.p, st);
+      CK(cudaMemcpyAsync(grad_b, B.Bu.p, sizeof(double) * h->m * R, cudaMemcpyDeviceToHost, st));
+    }
+    launches += 1;
+  }
+  if (grad_vals) {
+    // x interleaved into Z, b into B, rho = b - A x into Bu
+    lsq::launch_b_load_cols(h->n, R, device_view(h, x, h->n, R), B.Z.p, st);
+    lsq::launch_b_load_rows(h->m, R, h->perm.p, device_view(h, b, h->m, R), B.B.p, st);
+    lsq::launch_b_spmm_csr(csr(h), B.Z.p, B.Bu.p, R, st);
+    lsq::launch_b_sub((int64_t)h->m * R, B.B.p, B.Bu.p, st);
+    DevBuf<double> gout;
+    gout.alloc(h->nnz);
+    lsq::launch_b_grad_vals(csr(h), h->entmap.p, R, B.Bu.p, B.X.p, B.Q.p, B.Z.p, gout.p, st);
+    CK(cudaMemcpyAsync(grad_vals, gout.p, sizeof(double) * h->nnz, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    launches += 5;
+  }
+  CK(cudaStreamSynchronize(st));
+  check_launch("block adjoint");
+  inf.launches = launches;
+  inf.t_solve = now_s() - t0;
+  if (info) *info = inf;
+  if (!ok)
+    throw LsError(LS_ERR_NOT_CONVERGED, "adjoint solve: maximum number of iterations reached, worst true relative "
+                                        "residual " + std::to_string(inf.relres_true));
   return LS_OK;
 }
 

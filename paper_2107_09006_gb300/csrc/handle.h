@@ -85,7 +85,7 @@ inline void check_launch(const char* what) {
 // number of right-hand sides they are sized for, vectors are interleaved [index][R].
 struct BlockState {
   int R = 0;
-  DevBuf<double> X, Rv, Rold, Z, P, W, Q, B, Y, R0, Y0, Bu;
+  DevBuf<double> X, Rv, Rold, Z, P, W, Q, B, Y, R0, Y0, Bu, G;
   DevBuf<unsigned char> Vg;          // forward-sweep spill of the local solves
   DevBuf<double> parts, sc;          // chunk partials; per (problem, rhs) scalars
   DevBuf<int> act, its, stat;        // active mask, iterations, {nact, flag, err}
@@ -218,6 +218,10 @@ inline lsq::CscDev csc(const ls_handle* h) {
 
 // The multi right-hand-side PCG (block.cu): b [R][m] and x [R][n], host or device.
 ls_status block_solve(ls_handle* h, const double* b, int R, double rtol, double* x, ls_info* info);
+// The adjoint of the block path (block.cu): lambda = C^{-1} grad_x for every pair, then
+// grad_b = A lambda ([R][m]) and grad_vals summed over the pairs.
+ls_status block_backward(ls_handle* h, const double* b, const double* x, const double* grad_x, int R, double rtol,
+                         double* grad_b, double* grad_vals, ls_info* info);
 // Chunk tables, work order and coarse tiles of the block solve (block.cu), built by setup.
 void block_plan(ls_handle* h);
 

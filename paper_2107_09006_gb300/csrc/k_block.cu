@@ -446,6 +446,82 @@ __global__ void __launch_bounds__(kThreads) k_b_store_cols(int64_t n, int R, con
   }
 }
 
+// Xb[j * R + k] = Xu[k * n + j] (caller's column-major n-vectors -> interleaved), 32
+// columns per tile.
+__global__ void __launch_bounds__(kThreads) k_b_load_cols(int64_t n, int R, const double* __restrict__ Xu,
+                                                          double* __restrict__ Xb) {
+  __shared__ double t[32][33];
+  for (int64_t j0 = (int64_t)blockIdx.x * 32; j0 < n; j0 += (int64_t)gridDim.x * 32) {
+    const int cols = (int)(n - j0 < 32 ? n - j0 : 32);
+    for (int e = threadIdx.x; e < 32 * R; e += blockDim.x) {
+      const int k = e / 32, jj = e % 32;
+      if (jj < cols) t[jj][k] = Xu[(int64_t)k * n + j0 + jj];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cols * R; e += blockDim.x) Xb[j0 * R + e] = t[e / R][e % R];
+    __syncthreads();
+  }
+}
+
+// Yu[k * m + perm[r']] = Yb[r' * R + k] (interleaved rows of the row-reordered matrix ->
+// the caller's column-major m-vectors).
+__global__ void __launch_bounds__(kThreads) k_b_store_rows(int64_t m, int R, int Rp, const int32_t* __restrict__ perm,
+                                                           const double* __restrict__ Yb, double* __restrict__ Yu) {
+  const Lanes L(Rp);
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (L.k >= R) return;
+  for (int64_t r = wg * L.G + L.g; r < m; r += nw * L.G) Yu[(int64_t)L.k * m + perm[r]] = Yb[r * R + L.k];
+}
+
+// W = G - W with the per-chunk partials of W . W (the residual of C x = g when W = C x;
+// with W = 0 beforehand it copies G and gives ||G||^2).
+__global__ void __launch_bounds__(kThreads) k_b_resid(BChunks ch, int R, int Rp, const double* __restrict__ G,
+                                                      double* __restrict__ W, double* __restrict__ part) {
+  __shared__ double red[kWarps * 32];
+  const Lanes L(Rp);
+  const int w = threadIdx.x >> 5;
+  for (int64_t c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int64_t s = ch.start[c], e = ch.start[c + 1];
+    double d = 0.0;
+    if (L.k < R) {
+      for (int64_t j = s + w * L.G + L.g; j < e; j += kWarps * L.G) {
+        const int64_t x = j * R + L.k;
+        const double v = G[x] - W[x];
+        W[x] = v;
+        d += v * v;
+      }
+    }
+    chunk_total(d, Rp, R, red, part + c * 32);
+  }
+}
+
+// Gradient on the stored entries, summed over the right-hand sides: for entry e of row
+// r' of the row-reordered matrix (column c), out[entmap[e]] = sum_k rho[r', k] lam[c, k]
+// - (A lam)[r', k] x[c, k]; one warp per row, lane k per right-hand side.
+__global__ void __launch_bounds__(kThreads) k_b_grad_vals(int64_t m, const int64_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ col,
+                                                          const int64_t* __restrict__ entmap, int R,
+                                                          const double* __restrict__ rho,
+                                                          const double* __restrict__ lam,
+                                                          const double* __restrict__ Al,
+                                                          const double* __restrict__ X, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = wg; r < m; r += nw) {
+    const double rr = lane < R ? rho[r * R + lane] : 0.0;
+    const double ar = lane < R ? Al[r * R + lane] : 0.0;
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+      const int64_t c = col[e];
+      double v = lane < R ? rr * lam[c * R + lane] - ar * X[c * R + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) out[entmap[e]] = v;
+    }
+  }
+}
+
 __global__ void k_b_sub(int64_t len, const double* __restrict__ a, double* __restrict__ b) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
     b[e] = a[e] - b[e];
@@ -1106,6 +1182,25 @@ void launch_b_load_rows(int64_t m, int R, const int32_t* perm, const double* Bu,
 void launch_b_store_cols(int64_t n, int R, const double* Xb, double* Xu, cudaStream_t st) {
   const int64_t tiles = (n + 31) / 32;
   k_b_store_cols<<<(int)(tiles > 65536 ? 65536 : tiles), kThreads, 0, st>>>(n, R, Xb, Xu);
+}
+
+void launch_b_load_cols(int64_t n, int R, const double* Xu, double* Xb, cudaStream_t st) {
+  const int64_t tiles = (n + 31) / 32;
+  k_b_load_cols<<<(int)(tiles > 65536 ? 65536 : tiles), kThreads, 0, st>>>(n, R, Xu, Xb);
+}
+
+void launch_b_store_rows(int64_t m, int R, const int32_t* perm, const double* Yb, double* Yu, cudaStream_t st) {
+  const int Rp = pow2_at_least(R);
+  k_b_store_rows<<<grid_rows(m, 32 / Rp), kThreads, 0, st>>>(m, R, Rp, perm, Yb, Yu);
+}
+
+void launch_b_resid(const BChunks& ch, int R, const double* G, double* W, double* part, cudaStream_t st) {
+  k_b_resid<<<grid_chunks(ch.n), kThreads, 0, st>>>(ch, R, pow2_at_least(R), G, W, part);
+}
+
+void launch_b_grad_vals(const CsrDev& A, const int64_t* entmap, int R, const double* rho, const double* lam,
+                        const double* Al, const double* X, double* out, cudaStream_t st) {
+  k_b_grad_vals<<<grid_rows(A.m, 1), kThreads, 0, st>>>(A.m, A.row_ptr, A.col, entmap, R, rho, lam, Al, X, out);
 }
 
 void launch_b_sub(int64_t len, const double* a, double* b, cudaStream_t st) {

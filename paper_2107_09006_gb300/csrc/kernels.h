@@ -229,5 +229,15 @@ void launch_b_load_rows(int64_t m, int R, const int32_t* perm, const double* Bu,
 void launch_b_store_cols(int64_t n, int R, const double* Xb, double* Xu, cudaStream_t st);
 // b = a - b over len entries
 void launch_b_sub(int64_t len, const double* a, double* b, cudaStream_t st);
+// Xb = interleaved copy of the caller's column-major n-vectors Xu ([R][n])
+void launch_b_load_cols(int64_t n, int R, const double* Xu, double* Xb, cudaStream_t st);
+// Yu[k * m + perm[r]] = Yb[r * R + k]
+void launch_b_store_rows(int64_t m, int R, const int32_t* perm, const double* Yb, double* Yu, cudaStream_t st);
+// W = G - W and the chunk partials of W . W
+void launch_b_resid(const BChunks& ch, int R, const double* G, double* W, double* part, cudaStream_t st);
+// gradient on the stored entries of A (caller's CSR order through entmap), summed over
+// the R right-hand sides: rho lam^T - (A lam) x^T sampled on the pattern
+void launch_b_grad_vals(const CsrDev& A, const int64_t* entmap, int R, const double* rho, const double* lam,
+                        const double* Al, const double* X, double* out, cudaStream_t st);
 
 }  // namespace lsq
