@@ -37,6 +37,7 @@ from .schwarz import (  # noqa: F401
     lanczos_kappa,
     preconditioned_lsqr,
     lsqr_kappa,
+    fgmres,
     adjoint_gradient,
     multiplicity_km,
     colouring_kc,

@@ -277,6 +277,47 @@ def test_preconditioned_lsqr(tiny):
     assert abs(kl - kp) <= 1e-6 * kp
 
 
+# --------------------------------------------------------------------------- RAS, deflated, GMRES
+def test_ras_deflated_and_fgmres(tiny):
+    """RAS (Section 2): the D_i form a partition of unity (sum_i R_i^T D_i R_i = I) and
+    with one subdomain RAS is the exact inverse of C + delta I; the deflated operator
+    Q + M_RAS (I - CQ) inverts C on the coarse space (delta = 0); GMRES's iterates are
+    the minimisers of ||A^T b - C x|| over independently built (preconditioned) Krylov
+    bases, and it reaches the least-squares solution."""
+    A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
+    C = (A.T @ A).toarray()
+    g = A.T @ tiny.b
+    M = O.build_two_level(A, tiny.part, tiny.nparts, tau=0.0, nev_max=16)
+    cover = np.zeros(tiny.n)
+    for i in range(tiny.nparts):
+        R = restriction(M.S.Om[i], tiny.n)
+        d = np.isin(M.S.Om[i], M.S.OI[i]).astype(float)
+        cover += R.T @ d
+    assert np.array_equal(cover, np.ones(tiny.n))
+    M1 = O.build_two_level(A, np.zeros(tiny.n, np.int32), 1, tau=0.6, nev_max=16)
+    r = np.random.default_rng(5).standard_normal(tiny.n)
+    assert np.allclose(M1.apply_ras(r), np.linalg.solve(C + M1.delta * np.eye(tiny.n), r), rtol=1e-9)
+    M0 = O.build_two_level(A, tiny.part, tiny.nparts, tau=0.0, nev_max=16, delta_rel=0.0)
+    R0T = M0.R0T.toarray()
+    for j in range(0, R0T.shape[1], 7):
+        z = M0.apply_deflated(A, C @ R0T[:, j])
+        assert np.linalg.norm(z - R0T[:, j]) <= 1e-10 * np.linalg.norm(R0T[:, j])
+    for apply in (lambda v: v, lambda v: M.apply_deflated(A, v)):
+        for k in (1, 3, 5):
+            x, _ = O.fgmres(A, tiny.b, apply, fixed_iters=k)
+            cols, v = [], g.copy()
+            for _ in range(k):
+                z = apply(v)
+                cols.append(z)
+                v = C @ z
+            Qk, _ = np.linalg.qr(np.column_stack(cols))
+            xk = Qk @ np.linalg.lstsq(C @ Qk, g, rcond=None)[0]
+            assert np.linalg.norm(x - xk) <= 1e-10 * np.linalg.norm(xk)
+    x, info = O.fgmres(A, tiny.b, lambda v: M.apply_deflated(A, v), rtol=1e-10)
+    xl = np.linalg.lstsq(A.toarray(), tiny.b, rcond=None)[0]
+    assert info["relres_true"] <= 1e-10 and np.linalg.norm(x - xl) <= 1e-6 * np.linalg.norm(xl)
+
+
 # --------------------------------------------------------------------------- tau rule
 def test_auto_tau_and_cap(tiny):
     A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
