@@ -47,9 +47,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16"], help="headline form")
     ap.add_argument("--forms", default="f32,f64",
-                    help="forms to run (comma list of f32, f64, bf16; suffix 'b' (f32b) selects the balanced "
-                         "second level instead of the additive one, suffix 'l' (f32l, f32bl) the LSQR outer "
-                         "solver instead of PCG)")
+                    help="forms to run (comma list of f32, f64, bf16; suffixes: 'b' the balanced second level, "
+                         "'d' RAS with the deflated second level, 'l' the LSQR outer solver, 'g' GMRES(100); "
+                         "e.g. f32b, f32bl, f32dg)")
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--nev", type=int, default=32)
@@ -248,9 +248,10 @@ def run_ours(args):
             dist.barrier()
 
     for spec in forms:
-        form = spec.rstrip("bl")
-        variant = 1 if "b" in spec[len(form):] else 0
-        solver = 1 if "l" in spec[len(form):] else 0
+        form = spec.rstrip("bdlg")
+        suf = spec[len(form):]
+        variant = 1 if "b" in suf else 2 if "d" in suf else 0
+        solver = 1 if "l" in suf else 2 if "g" in suf else 0
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
                    nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,

@@ -84,14 +84,20 @@ typedef struct {
     int variant;       /* second level: 0 additive (eq. (2.3), the default); 1 balanced,
                           Q + (I - CQ)^T M_1 (I - CQ) with Q = R_0^T C_00^{-1} R_0 and the
                           one-level M_1 (Section 2): two more products with C and one
-                          more coarse correction per apply.  Single-problem handles and
-                          one right-hand side only (else LS_ERR_UNSUPPORTED).          */
+                          more coarse correction per apply; 2 deflated with the
+                          restricted first level (RAS, each column takes the solution
+                          of its own subdomain only), Q + M_RAS (I - CQ): not symmetric,
+                          so it needs solver = 2 (GMRES).  1 and 2: single-problem
+                          handles, one right-hand side (else LS_ERR_UNSUPPORTED).      */
     int solver;        /* outer Krylov method of ls_solve: 0 PCG on the normal equations
                           (the default); 1 LSQR preconditioned with M^{-1} (the paper's
                           solver, Section 4.1.3): Golub-Kahan bidiagonalization in the
                           inner product of M, one preconditioner apply per iteration,
-                          the same stopping test on the true residual.  Single problem,
-                          one right-hand side; ls_backward always uses PCG.           */
+                          the same stopping test on the true residual; 2 restarted
+                          GMRES on C x = A^T b, right-preconditioned (flexible form),
+                          restart length `restart`.  1 and 2: single problem, one
+                          right-hand side; ls_backward always uses PCG.               */
+    int restart;       /* GMRES restart length (default 100, as in Section 4)          */
 } ls_options;
 
 typedef struct {
@@ -123,7 +129,7 @@ typedef struct ls_handle ls_handle;
 /* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
- * equilibrate = 0, variant = 0, solver = 0. */
+ * equilibrate = 0, variant = 0, solver = 0, restart = 100. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping

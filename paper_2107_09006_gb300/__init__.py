@@ -27,7 +27,8 @@ class ls_options(ctypes.Structure):
                 ("s_rel", ctypes.c_double), ("factor_prec", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int),
+                ("restart", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):

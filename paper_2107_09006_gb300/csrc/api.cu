@@ -153,10 +153,35 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
                        dots ? site(h, lsq::S_RZ, 2, lsq::S_RZO - lsq::S_RZ) : lsq::DotSite{}, st);
 }
 
+// z = Q r + M_RAS (I - C Q) r (the deflated second level of Section 2 with the RAS first
+// level; without a coarse space, z = M_RAS r).  No fused dots: only GMRES uses it.
+void precond_deflated(ls_handle* h, const double* rin, double* zout, bool timed) {
+  cudaStream_t st = h->st;
+  const bool coarse = h->coarse && h->n0 > 0;
+  const double* t = rin;
+  if (coarse) {
+    coarse_term(h, rin, h->bal_y.p);                                     // Q r
+    apply_C(h, h->bal_y.p, h->bal_t.p);                                  // C Q r
+    lsq::launch_axpby(h->n, 1.0, rin, -1.0, h->bal_t.p, h->bal_t.p, st);  // (I - CQ) r
+    t = h->bal_t.p;
+  }
+  if (timed) record_event(h->ev[2], st);
+  launch_local(h, t, false);
+  if (timed) record_event(h->ev[3], st);
+  lsq::launch_ras_combine(h->n, h->own.p, h->ybuf.p, coarse ? h->bal_y.p : nullptr, zout, st);
+  if (timed) record_event(h->ev[4], st);
+}
+
+int deflated_launches(const ls_handle* h) { return 2 + ((h->coarse && h->n0 > 0) ? 6 : 0); }
+
 // z = M^{-1} r (which: 0 both terms, 1 local only, 2 coarse only) with the fused dots
 // r.z (and r_old.z for the flexible recurrence) into the partial arrays.
 void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots, bool flex, bool timed = false) {
   cudaStream_t st = h->st;
+  if (which == 0 && h->opt.variant == 2) {
+    precond_deflated(h, rin, zout, timed);
+    return;
+  }
   if (which == 0 && balanced(h)) {
     precond_balanced(h, rin, zout, dots, flex, timed);
     return;
@@ -497,6 +522,143 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
   return finish(it, converged, rel);
 }
 
+// Restarted GMRES on C x = A^T b' (b' in h->bv, result in h->x), right-preconditioned in
+// the flexible form (z_j = M^{-1} v_j kept): Arnoldi with classical Gram-Schmidt applied
+// twice (multi-vector dot and update kernels, deterministic), Givens rotations on the
+// host.  |gamma_{j+1}| = ||A^T b - C x_j||, the configs' residual; a pass (or the end of
+// a cycle) updates x, and every cycle starts from the true residual, which confirms
+// the pass.
+ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  const int mr = h->opt.restart;
+  const double t0 = now_s();
+  ls_info inf{};
+  inf.bad_subdomain = -1;
+  int launches = 0;
+  lsq::launch_spmv_csc(csc(h), h->bv.p, h->gm_g.p, nullptr, site(h, lsq::S_TMP, 0), h->lanes_csc, h->grid_csc, st);
+  const double gg = dev_sum(h);
+  launches += 1;
+  if (!std::isfinite(gg)) throw LsError(LS_ERR_NONFINITE, "right-hand side is not finite");
+  const double gn = std::sqrt(gg);
+  lsq::launch_fill(n, 0.0, h->x.p, st);
+  CK(cudaMemsetAsync(h->scal.p, 0, sizeof(double) * lsq::S_NSLOT, st));
+  launches += 1;
+  const bool timed = h->opt.time_kernels != 0;
+  const int pl = h->opt.variant == 2 ? deflated_launches(h)
+               : balanced(h) ? kBalancedLaunches : 2 + ((h->coarse && h->n0 > 0) ? 1 : 0);
+  const int fixed = h->opt.fixed_iters;
+  const int maxit = fixed > 0 ? fixed : h->opt.maxit;
+  std::vector<double> H((size_t)(mr + 1) * mr, 0.0), cs(mr), sn(mr), gam(mr + 1), hv(2 * (size_t)(mr + 1));
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * mr + j]; };
+  double* V = h->gm_V.p;
+  double* Z = h->gm_Z.p;
+  double* h1 = h->gm_h.p;
+  double* h2 = h->gm_h.p + (mr + 1);
+  double* yv = h->gm_h.p + 2 * (mr + 1);
+  int it = 0;
+  bool converged = false;
+  double rel = 1.0;
+  while (true) {
+    // r = A^T b - C x into V(:, 0)
+    apply_C(h, h->x.p, h->w.p);
+    lsq::launch_axpby(n, 1.0, h->gm_g.p, -1.0, h->w.p, V, st);
+    lsq::launch_dot(n, V, V, site(h, lsq::S_TMP, 3), st);
+    const double beta = std::sqrt(dev_sum(h));
+    launches += 4;
+    rel = gn > 0.0 ? beta / gn : 0.0;
+    if (fixed <= 0 && beta <= rtol * gn) {
+      converged = true;
+      break;
+    }
+    if ((fixed > 0 && it >= fixed) || (fixed <= 0 && it >= maxit)) break;
+    if (!std::isfinite(beta)) throw LsError(LS_ERR_NONFINITE, "GMRES: non-finite residual");
+    lsq::launch_axpby(n, 1.0 / beta, V, 0.0, nullptr, V, st);
+    std::fill(gam.begin(), gam.end(), 0.0);
+    gam[0] = beta;
+    int j = 0;
+    while (j < mr) {
+      double* vj = V + (int64_t)j * n;
+      double* zj = Z + (int64_t)j * n;
+      double* w = V + (int64_t)(j + 1) * n;
+      if (timed) record_event(h->ev[0], st);
+      precond(h, vj, zj, 0, false, false, timed);
+      apply_C(h, zj, w);
+      if (timed) record_event(h->ev[1], st);
+      lsq::launch_multi_dot(n, V, n, j + 1, w, h->gm_part.p, h1, st);
+      lsq::launch_multi_axpy(n, V, n, j + 1, h1, -1.0, w, st);
+      lsq::launch_multi_dot(n, V, n, j + 1, w, h->gm_part.p, h2, st);
+      lsq::launch_multi_axpy(n, V, n, j + 1, h2, -1.0, w, st);
+      lsq::launch_dot(n, w, w, site(h, lsq::S_TMP, 3), st);
+      CK(cudaMemcpyAsync(hv.data(), h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hv.data() + (mr + 1), h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+      const double hn = std::sqrt(dev_sum(h));  // synchronises the stream
+      if (dev_sum(h, lsq::S_ERR) != 0.0)
+        throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up at iteration " +
+                                                 std::to_string(it + 1));
+      if (!std::isfinite(hn)) throw LsError(LS_ERR_NONFINITE, "GMRES breakdown at iteration " + std::to_string(it + 1));
+      if (timed) {
+        record_event(h->ev[5], st);
+        CK(cudaStreamSynchronize(st));
+        float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
+        CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[1]));
+        CK(cudaEventElapsedTime(&tb, h->ev[2], h->ev[3]));
+        CK(cudaEventElapsedTime(&tc, h->ev[3], h->ev[4]));
+        CK(cudaEventElapsedTime(&td, h->ev[0], h->ev[5]));
+        inf.ms_spmv += ta; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
+      }
+      for (int i = 0; i <= j; ++i) Hat(i, j) = hv[i] + hv[(mr + 1) + i];
+      Hat(j + 1, j) = hn;
+      if (hn > 0.0) lsq::launch_axpby(n, 1.0 / hn, w, 0.0, nullptr, w, st);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
+        Hat(i + 1, j) = -sn[i] * Hat(i, j) + cs[i] * Hat(i + 1, j);
+        Hat(i, j) = t;
+      }
+      const double den = std::hypot(Hat(j, j), Hat(j + 1, j));
+      cs[j] = Hat(j, j) / den;
+      sn[j] = Hat(j + 1, j) / den;
+      Hat(j, j) = den;
+      Hat(j + 1, j) = 0.0;
+      gam[j + 1] = -sn[j] * gam[j];
+      gam[j] = cs[j] * gam[j];
+      ++j;
+      ++it;
+      launches += pl + 2 + 4 * 2 + 1 + (hn > 0.0 ? 1 : 0);
+      inf.local_launches += 1;
+      if (fixed > 0 && it >= fixed) break;
+      if (fixed <= 0 && (std::fabs(gam[j]) <= rtol * gn || it >= maxit)) break;
+      if (!(hn > 0.0)) break;  // the Krylov space is invariant: the cycle's solution is exact
+    }
+    // x += Z y, H(0:j, 0:j) y = gamma(0:j)
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = gam[i];
+      for (int k = i + 1; k < j; ++k) s -= Hat(i, k) * y[k];
+      y[i] = s / Hat(i, i);
+    }
+    CK(cudaMemcpyAsync(yv, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+    lsq::launch_multi_axpy(n, Z, n, j, yv, 1.0, h->x.p, st);
+    CK(cudaStreamSynchronize(st));
+    launches += 1;
+  }
+  check_launch("GMRES");
+  inf.iters = it;
+  inf.relres_true = rel;
+  inf.relres_recursive = rel;
+  inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
+  inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
+  inf.eig_steps_max = h->sinfo.eig_steps_max;
+  inf.launches = launches;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  inf.t_solve = now_s() - t0;
+  if (info) *info = inf;
+  if (!converged && fixed <= 0)
+    return (g_err = "maximum number of iterations reached, true relative residual " + std::to_string(rel),
+            LS_ERR_NOT_CONVERGED);
+  return LS_OK;
+}
+
 template <class F>
 ls_status guarded(F&& f) {
   try {
@@ -710,6 +872,13 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
       for (int64_t a = hs.int_off[i]; a < hs.int_off[i + 1]; ++a)
         ig[a] = hs.om_glob[hs.om_off[i] + hs.int_loc[a]];
     h->int_glob.upload(ig, st);
+    if (h->opt.variant == 2) {
+      // RAS: the local-solution entry that column j takes from its own subdomain
+      std::vector<int64_t> own(h->n, 0);
+      for (int i = 0; i < N; ++i)
+        for (int64_t a = hs.int_off[i]; a < hs.int_off[i + 1]; ++a) own[ig[a]] = hs.om_off[i] + hs.int_loc[a];
+      h->own.upload(own, st);
+    }
   }
   DevBuf<int32_t> row_sub;
   {
@@ -982,8 +1151,16 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->r0.alloc(std::max<int64_t>(h->n0p, 1)); h->r0.zero(st);
   h->y0.alloc(std::max<int64_t>(h->n0p, 1)); h->y0.zero(st);
   h->tv.alloc(h->n); h->bv.alloc(h->m);
-  if (h->opt.variant == 1) {
+  if (h->opt.variant == 1 || h->opt.variant == 2) {
     h->bal_y.alloc(h->n); h->bal_t.alloc(h->n); h->bal_u.alloc(h->n); h->bal_v.alloc(h->n);
+  }
+  if (h->opt.solver == 2) {
+    const int mr = h->opt.restart;
+    h->gm_V.alloc((size_t)h->n * (mr + 1));
+    h->gm_Z.alloc((size_t)h->n * mr);
+    h->gm_g.alloc(h->n);
+    h->gm_h.alloc(3 * (size_t)(mr + 1));
+    h->gm_part.alloc((size_t)lsq::multi_dot_grid(h->n) * (mr + 1));
   }
   if (h->opt.solver == 1) {
     h->lq_u.alloc(h->m);
@@ -1026,6 +1203,7 @@ void ls_default_options(ls_options* o) {
   o->equilibrate = 0;
   o->variant = 0;
   o->solver = 0;
+  o->restart = 100;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1048,10 +1226,14 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.factor_prec < 0 || h->opt.factor_prec > 2) throw LsError(LS_ERR_INVALID, "bad factor_prec");
     if (h->opt.maxit < 1 && h->opt.fixed_iters < 1) throw LsError(LS_ERR_INVALID, "maxit must be positive");
     if (h->opt.nev_max < 0) throw LsError(LS_ERR_INVALID, "nev_max must be >= 0");
-    if (h->opt.variant < 0 || h->opt.variant > 1) throw LsError(LS_ERR_INVALID, "variant must be 0 or 1");
-    if (h->opt.solver < 0 || h->opt.solver > 1) throw LsError(LS_ERR_INVALID, "solver must be 0 or 1");
-    if (h->opt.variant == 1 && nprob > 1)
-      throw LsError(LS_ERR_UNSUPPORTED, "the balanced variant is implemented for single-problem handles");
+    if (h->opt.variant < 0 || h->opt.variant > 2) throw LsError(LS_ERR_INVALID, "variant must be 0, 1 or 2");
+    if (h->opt.solver < 0 || h->opt.solver > 2) throw LsError(LS_ERR_INVALID, "solver must be 0, 1 or 2");
+    if (h->opt.variant == 2 && h->opt.solver != 2)
+      throw LsError(LS_ERR_INVALID, "the deflated RAS variant is not symmetric: it needs solver = 2 (GMRES)");
+    if (h->opt.solver == 2 && (h->opt.restart < 1 || h->opt.restart > 1000))
+      throw LsError(LS_ERR_INVALID, "restart must lie in [1, 1000]");
+    if (h->opt.variant != 0 && nprob > 1)
+      throw LsError(LS_ERR_UNSUPPORTED, "the balanced and deflated variants are implemented for single-problem handles");
     if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
     CK(cudaGetDevice(&h->dev));
     if (stream) {
@@ -1109,7 +1291,8 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
     CK(cudaSetDevice(h->dev));
     if (nrhs > 1 || h->nprob > 1) {
       if (h->opt.solver != 0)
-        throw LsError(LS_ERR_UNSUPPORTED, "the LSQR outer solver takes one right-hand side of a single problem");
+        throw LsError(LS_ERR_UNSUPPORTED, "the LSQR and GMRES outer solvers take one right-hand side of a single "
+                                          "problem");
       return block_solve(h, b, nrhs, rtol, x, info);
     }
     ls_status last = LS_OK;
@@ -1117,7 +1300,8 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
       // b' = P b for the row-reordered device matrix
       CK(cudaMemcpyAsync(h->q.p, b + (int64_t)k * h->m, sizeof(double) * h->m, cudaMemcpyDefault, h->st));
       lsq::launch_gather(h->m, h->perm.p, h->q.p, h->bv.p, h->st);
-      ls_status s = h->opt.solver == 1 ? lsqr_core(h, rtol, info) : solve_core(h, 0, rtol, info);
+      ls_status s = h->opt.solver == 1 ? lsqr_core(h, rtol, info)
+                  : h->opt.solver == 2 ? gmres_core(h, rtol, info) : solve_core(h, 0, rtol, info);
       CK(cudaMemcpyAsync(x + (int64_t)k * h->n, h->x.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
       CK(cudaStreamSynchronize(h->st));
       if (s != LS_OK) last = s;

@@ -163,6 +163,8 @@ struct ls_handle {
   DevBuf<double> x, r, r_old, z, p, q, w, ybuf, r0, y0, tv, bv;
   DevBuf<double> bal_y, bal_t, bal_u, bal_v;  // work vectors of the balanced variant
   DevBuf<double> lq_u, lq_v, lq_q, lq_s, lq_t, lq_w;  // LSQR: u (m), v, M v, s, M^{-1} s, w
+  DevBuf<int64_t> own;                                // RAS: local entry of column j in its own subdomain
+  DevBuf<double> gm_V, gm_Z, gm_g, gm_h, gm_part;     // GMRES: Arnoldi basis, M^{-1} basis, A^T b, coefs
   DevBuf<double> parts, scal, ahist, bhist;
   DevBuf<unsigned> counters;  // ticket counters of the fused reductions
   DevBuf<int> ctr;

@@ -339,6 +339,52 @@ __global__ void __launch_bounds__(kThreads) k_lsqr_step(int64_t n, double inv_al
   }
 }
 
+// RAS prolongation: z_j = a_j + y[own[j]] (a may be null), the local solution of the
+// subdomain that owns column j only.
+__global__ void __launch_bounds__(kThreads) k_ras_combine(int64_t n, const int64_t* __restrict__ own,
+                                                          const double* __restrict__ y, const double* __restrict__ a,
+                                                          double* __restrict__ z) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    z[j] = (a ? a[j] : 0.0) + y[own[j]];
+}
+
+// Per-block partial dots of the k columns of V (column-major, leading dimension ld)
+// with w: part[c * gridDim.x + block] (one column after another, block-wide sums).
+__global__ void __launch_bounds__(kThreads) k_multi_dot(int64_t n, const double* __restrict__ V, int64_t ld, int k,
+                                                        const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double red[kWarps];
+  for (int c = 0; c < k; ++c) {
+    double acc = 0.0;
+    const double* v = V + (int64_t)c * ld;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+      acc += v[r] * w[r];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)c * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// out[c] = sum of column c's partials in block order (one block per column).
+__global__ void __launch_bounds__(kThreads) k_multi_dot_finish(int nparts, const double* __restrict__ part,
+                                                               double* __restrict__ out) {
+  __shared__ double red[kWarps];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) acc += part[(int64_t)c * nparts + b];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[c] = acc;
+}
+
+// out += sign * V coef over the k columns of V (column-major, leading dimension ld).
+__global__ void __launch_bounds__(kThreads) k_multi_axpy(int64_t n, const double* __restrict__ V, int64_t ld, int k,
+                                                         const double* __restrict__ coef, double sign,
+                                                         double* __restrict__ out) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < k; ++c) acc += V[(int64_t)c * ld + r] * coef[c];
+    out[r] += sign * acc;
+  }
+}
+
 // y0 = X r0 for the dense n0 x n0 coarse inverse (one warp per row).
 __global__ void __launch_bounds__(kThreads) k_gemv(int64_t n0, const double* __restrict__ X,
                                                    const double* __restrict__ r0, double* __restrict__ y0) {
@@ -470,6 +516,24 @@ void launch_scatter_idx(int64_t n, const int32_t* idx32, const int64_t* idx64, c
 void launch_lsqr_step(int64_t n, double inv_alpha, double c1, double c2, const double* t, const double* s, double* v,
                       double* q, double* x, double* w, cudaStream_t st) {
   k_lsqr_step<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, inv_alpha, c1, c2, t, s, v, q, x, w);
+}
+
+void launch_ras_combine(int64_t n, const int64_t* own, const double* y, const double* a, double* z, cudaStream_t st) {
+  k_ras_combine<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, own, y, a, z);
+}
+
+int multi_dot_grid(int64_t n) { return grid_for(n, kThreads * 4, kVecGrid); }
+
+void launch_multi_dot(int64_t n, const double* V, int64_t ld, int k, const double* w, double* part, double* out,
+                      cudaStream_t st) {
+  const int g = multi_dot_grid(n);
+  k_multi_dot<<<g, kThreads, 0, st>>>(n, V, ld, k, w, part);
+  k_multi_dot_finish<<<k, kThreads, 0, st>>>(g, part, out);
+}
+
+void launch_multi_axpy(int64_t n, const double* V, int64_t ld, int k, const double* coef, double sign, double* out,
+                       cudaStream_t st) {
+  k_multi_axpy<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, V, ld, k, coef, sign, out);
 }
 
 void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,

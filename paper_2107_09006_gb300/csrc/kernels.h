@@ -73,6 +73,16 @@ void launch_scatter(const ScatterArgs& a, cudaStream_t st);
 // w = v - c2 w.
 void launch_lsqr_step(int64_t n, double inv_alpha, double c1, double c2, const double* t, const double* s, double* v,
                       double* q, double* x, double* w, cudaStream_t st);
+// RAS prolongation z_j = a_j + y[own[j]] (a may be null)
+void launch_ras_combine(int64_t n, const int64_t* own, const double* y, const double* a, double* z, cudaStream_t st);
+// out[c] = V(:, c) . w for the k columns of V (column-major, ld); part holds
+// multi_dot_grid(n) * k partial sums (deterministic order)
+int multi_dot_grid(int64_t n);
+void launch_multi_dot(int64_t n, const double* V, int64_t ld, int k, const double* w, double* part, double* out,
+                      cudaStream_t st);
+// out += sign * V coef (V column-major, ld; coef on the device)
+void launch_multi_axpy(int64_t n, const double* V, int64_t ld, int k, const double* coef, double sign, double* out,
+                       cudaStream_t st);
 // r0 = R_0 v (coarse restriction alone, FP64)
 void launch_restrict(int N, const int64_t* int_off, const int32_t* int_glob, const int64_t* zoff, const int32_t* coff,
                      const double* Z, const double* v, double* r0, cudaStream_t st);
