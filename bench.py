@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16"], help="headline form")
-    ap.add_argument("--forms", default="f32,f64",
+    ap.add_argument("--forms", default="f32,f64,f32dg",
                     help="forms to run (comma list of f32, f64, bf16; suffixes: 'b' the balanced second level, "
                          "'d' RAS with the deflated second level, 'l' the LSQR outer solver, 'g' GMRES(100); "
                          "e.g. f32b, f32bl, f32dg)")
