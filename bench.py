@@ -368,8 +368,8 @@ def run_nsweep(args):
     """Subdomain-count sweep on the n = 1M grid: for blocks of 128, 64 and 32 columns a
     side (N = 64, 256, 1024) the setup split (index sets + factors, eigensolve + coarse),
     n0, iterations to rtol and the solve time of the two-level additive form, plus the
-    iterations of the one-level method and of the balanced form; one JSON line per N and
-    a summary."""
+    iterations of the one-level method, of the balanced form and of GMRES with RAS and
+    the deflated second level; one JSON line per N and a summary."""
     torch, dev = _device_setup()
     from paper_2107_09006_gb300 import Solver, ls_solve
     from workloads import config_scale
@@ -421,8 +421,10 @@ def run_nsweep(args):
         torch.cuda.empty_cache()
         i1, k1, s1 = iters_of(P, b, x, stream, coarse=0, nev_max=0)
         ib, kb, sb = iters_of(P, b, x, stream, nev_max=args.nev, variant=1)
+        idg, _, sdg = iters_of(P, b, x, stream, nev_max=args.nev, variant=2, solver=2)
         row.update({"one_level": {"iterations": i1, "kappa_lanczos": k1, "solve_s": s1},
-                    "balanced": {"iterations": ib, "kappa_lanczos": kb, "solve_s": sb}})
+                    "balanced": {"iterations": ib, "kappa_lanczos": kb, "solve_s": sb},
+                    "deflated_ras_gmres": {"iterations": idg, "solve_s": sdg}})
         log(f"[nsweep] {json.dumps(row)}")
         rows.append(row)
     its = [r["iterations"] for r in rows]
