@@ -98,6 +98,12 @@ typedef struct {
                           restart length `restart`.  1 and 2: single problem, one
                           right-hand side; ls_backward always uses PCG.               */
     int restart;       /* GMRES restart length (default 100, as in Section 4)          */
+    int spmv;          /* kernel of the products with A and A^T: 0 (the default) times
+                          every candidate at setup and keeps the fastest for each;
+                          otherwise one code for both: 1, 2, 4, 8, 16, 32 lanes per
+                          row; -1 / -3 warp-stream (16 / 32 rows per warp); -2 sliced
+                          ELL (LS_ERR_INVALID else).  ls_info.lanes_csr / lanes_csc
+                          report the codes in use.                                    */
 } ls_options;
 
 typedef struct {
@@ -121,7 +127,7 @@ typedef struct {
     int local_launches;      /* local-solve launches of the last solve                      */
     int launches;            /* kernels launched by the last solve (all of this library's)  */
     double ms_iter;          /* with time_kernels: total ms of whole CG iterations (kernels) */
-    int lanes_csr, lanes_csc;/* lanes per row of A / per column of A^T chosen by the tuner  */
+    int lanes_csr, lanes_csc;/* kernel codes of the products with A / A^T (option spmv)    */
 } ls_info;
 
 typedef struct ls_handle ls_handle;

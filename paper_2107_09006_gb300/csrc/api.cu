@@ -715,15 +715,18 @@ void autotune_spmv(ls_handle* h) {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     return ms;
   };
+  const int forced = h->opt.spmv;
   float best = 1e30f;
-  // candidates: -2 sliced ELL, -1 / 0 warp-stream (16 / 32 rows per warp), 1..32 lanes per row
-  const int cand[] = {-2, -1, 0, 1, 2, 4, 8, 16, 32};
+  // candidates (kernel codes of kernels.h): sliced ELL, warp-stream, lanes per row
+  const int cand[] = {-2, -1, -3, 1, 2, 4, 8, 16, 32};
   for (int lanes : cand) {
+    if (forced != 0 && lanes != forced) continue;
     const float ms = time_it([&] { lsq::launch_spmv_csr(csr(h), xa.p, ya.p, lanes, 0, st); });
     if (ms < best) { best = ms; h->lanes_csr = lanes; }
   }
   best = 1e30f;
   for (int lanes : cand) {
+    if (forced != 0 && lanes != forced) continue;
     const float ms = time_it([&] { lsq::launch_spmv_csc(csc(h), xa.p, ya.p, nullptr, lsq::DotSite{}, lanes, 0, st); });
     if (ms < best) { best = ms; h->lanes_csc = lanes; }
   }
@@ -1204,6 +1207,7 @@ void ls_default_options(ls_options* o) {
   o->variant = 0;
   o->solver = 0;
   o->restart = 100;
+  o->spmv = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1232,6 +1236,8 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
       throw LsError(LS_ERR_INVALID, "the deflated RAS variant is not symmetric: it needs solver = 2 (GMRES)");
     if (h->opt.solver == 2 && (h->opt.restart < 1 || h->opt.restart > 1000))
       throw LsError(LS_ERR_INVALID, "restart must lie in [1, 1000]");
+    if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))
+      throw LsError(LS_ERR_INVALID, "spmv must be 0 or a sparse-product kernel code");
     if (h->opt.variant != 0 && nprob > 1)
       throw LsError(LS_ERR_UNSUPPORTED, "the balanced and deflated variants are implemented for single-problem handles");
     if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");

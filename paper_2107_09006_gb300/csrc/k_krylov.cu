@@ -431,10 +431,10 @@ void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int
     k_spmv_sell<<<grid, kThreads, 0, st>>>(A.sell, x, y, nullptr, DotSite{});
     return;
   }
-  if (lanes <= 0) {
-    const int R = lanes == 0 ? 32 : 16;
+  if (lanes < 0) {
+    const int R = lanes == -3 ? 32 : 16;
     if (grid <= 0) grid = grid_for((A.m + R - 1) / R, kWarps, kMaxGrid);
-    if (lanes == 0) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(A.m, A.row_ptr, A.col, A.val, x, y, nullptr, DotSite{});
+    if (lanes == -3) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(A.m, A.row_ptr, A.col, A.val, x, y, nullptr, DotSite{});
     else k_spmv_stream<16, 768><<<grid, kThreads, 0, st>>>(A.m, A.row_ptr, A.col, A.val, x, y, nullptr, DotSite{});
     return;
   }
@@ -456,10 +456,10 @@ void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double*
     k_spmv_sell<<<grid, kThreads, 0, st>>>(At.sell, q, w, d, ds);
     return;
   }
-  if (lanes <= 0) {
-    const int R = lanes == 0 ? 32 : 16;
+  if (lanes < 0) {
+    const int R = lanes == -3 ? 32 : 16;
     if (grid <= 0) grid = grid_for((At.n + R - 1) / R, kWarps, kMaxGrid);
-    if (lanes == 0) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(At.n, At.col_ptr, At.row, At.val, q, w, d, ds);
+    if (lanes == -3) k_spmv_stream<32, 512><<<grid, kThreads, 0, st>>>(At.n, At.col_ptr, At.row, At.val, q, w, d, ds);
     else k_spmv_stream<16, 768><<<grid, kThreads, 0, st>>>(At.n, At.col_ptr, At.row, At.val, q, w, d, ds);
     return;
   }

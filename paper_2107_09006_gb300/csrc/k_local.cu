@@ -119,19 +119,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   const int ni = (int)(a.om_off[i + 1] - o0);
   const int64_t b0 = a.blk_off[i];
   const int nb = (int)(a.blk_off[i + 1] - b0);
-  const int32_t* tf = a.blk_tf + b0;
-  const int64_t* poff = a.blk_poff + b0;
   const TF* fac = reinterpret_cast<const TF*>(a.fac);
   if (nb == 0) return;  // (the host rejects empty subdomains; kept as a guard)
+  // The block metadata (first tile column and storage offset of every block row) lives
+  // in shared memory behind v: it is read at every stage and block-row transition, and
+  // a global round trip there would sit on the dependency chain.
+  int64_t* poff = reinterpret_cast<int64_t*>(v + (size_t)nb * kT);  // 16-byte aligned
+  int32_t* tf = reinterpret_cast<int32_t*>(poff + nb);
+  for (int k = tid; k < nb; k += blockDim.x) {
+    poff[k] = a.blk_poff[b0 + k];
+    tf[k] = a.blk_tf[b0 + k];
+  }
 
   ChunkIter prod, cons;
-  int issued = 0;  // chunks issued so far (thread 0)
+  int issued = 0;  // chunks issued so far (issuing thread)
+  // The copies are issued by the last warp: warp 0 carries the diagonal products of the
+  // dependency chain, while the last warp's columns of a stage are most often the
+  // diagonal tile's, which the panel products skip.
+  const bool issuer = tid == kThreads - 32;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  __syncthreads();
+  __syncthreads();  // barriers initialised, block metadata staged
   auto issue = [&](int stage) {
     const int wd = prod.width(prod.b);
     const int hi = wd - prod.k * CC;
@@ -143,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     prod.next();
     ++issued;
   };
-  if (tid == 0) {
+  if (issuer) {
     prod.start(tf, nb, CC);
     for (int s = 0; s < S - 1 && !prod.done(); ++s) issue(s);
   }
@@ -167,11 +178,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   cons.start(tf, nb, CC);
   TA acc = 0;
   TA xr[kT];                                        // rotated copy of x_b (vectorised path)
-  const int rot = kVec ? (tid & (kT / XG - 1)) : 0;  // this thread's skew of 16-byte groups
+  // this thread's skew of 16-byte groups: consecutive threads read consecutive columns
+  // (32 x ES bytes each), so eight threads of a quarter-warp hit eight distinct 16-byte
+  // bank groups (BF16: two columns per 128 bytes, so the skew advances every other thread)
+  const int rot = kVec ? ((ES == 2 ? tid >> 1 : tid) & (kT / XG - 1)) : 0;
   int q = 0;
   while (!cons.done()) {
     const int stage = q % S;
-    if (tid == 0 && !prod.done()) issue((q + S - 1) % S);
+    if (issuer && !prod.done()) issue((q + S - 1) % S);
     {
       const uint32_t parity = (uint32_t)((q / S) & 1);
       if (!mbar_try_wait(&bars[stage], parity)) {
@@ -233,10 +247,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           tv[lane] = v[b * kT + lane] - s;
           __syncwarp();
           if (!kSplit) {
-            TA x = 0;
+            TA x0 = 0, x1 = 0;  // two FMA chains
 #pragma unroll 8
-            for (int c = 0; c < kT; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
-            v[b * kT + lane] = x * dsc;
+            for (int c = 0; c < kT; c += 2) {
+              x0 += Val<TF>::f(D[c * kT + lane]) * tv[c];
+              x1 += Val<TF>::f(D[(c + 1) * kT + lane]) * tv[c + 1];
+            }
+            v[b * kT + lane] = (x0 + x1) * dsc;
           }
         }
         if (kSplit) {  // FP64: the 32x32 product spread over the warps (the FP64 pipe is narrow)
@@ -262,13 +279,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
         __syncthreads();
         if (!kSplit) {
           if (w == 0) {
-            TA x = 0;
+            TA x0 = 0, x1 = 0;  // two FMA chains
 #pragma unroll 8
-            for (int u = 0; u < kT; ++u) {
-              const int r = (u + lane) & 31;  // skewed walk: no bank conflicts
-              x += Val<TF>::f(D[lane * kT + r]) * tv[r];
+            for (int u = 0; u < kT; u += 2) {
+              const int r0 = (u + lane) & 31, r1 = (u + 1 + lane) & 31;  // skewed walk: no bank conflicts
+              x0 += Val<TF>::f(D[lane * kT + r0]) * tv[r0];
+              x1 += Val<TF>::f(D[lane * kT + r1]) * tv[r1];
             }
-            x *= dsc;
+            TA x = (x0 + x1) * dsc;
             xv[lane] = x;
             v[b * kT + lane] = x;
           }
@@ -292,9 +310,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
         }
         __syncthreads();
         if constexpr (kVec) {
-          // this thread's copy of x_b, rotated like its skewed column reads
+          // this thread's copy of x_b, rotated like its skewed column reads (16-byte reads)
 #pragma unroll
-          for (int k = 0; k < kT; ++k) xr[k] = xv[(((k / XG) + rot) & (kT / XG - 1)) * XG + (k % XG)];
+          for (int g = 0; g < kT / XG; ++g)
+#pragma unroll
+            for (int h = 0; h < XG; h += 4) {
+              const float4 t = *reinterpret_cast<const float4*>(xv + ((g + rot) & (kT / XG - 1)) * XG + h);
+              xr[g * XG + h] = t.x; xr[g * XG + h + 1] = t.y; xr[g * XG + h + 2] = t.z; xr[g * XG + h + 3] = t.w;
+            }
         }
       }
       // v_window -= L_off^T x_b
@@ -361,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     ++q;
   }
   if (*abort_flag) {
-    if (tid == 0) {
+    if (issuer) {
       a.err[0] = 1.0;
       // bounded drain of the copies still in flight before the CTA's shared memory is released
       for (int qq = q; qq < issued; ++qq) {
@@ -429,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_to_solve_layout<__nv_bfloat16>(con
 
 template <class TF, class TA, int S>
 size_t smem_bytes(int max_nb) {
-  return v_offset<TA, S>() + (size_t)max_nb * kT * sizeof(TA);
+  return v_offset<TA, S>() + (size_t)max_nb * (kT * sizeof(TA) + sizeof(int64_t) + sizeof(int32_t));
 }
 
 template <class TF, class TA, int S>

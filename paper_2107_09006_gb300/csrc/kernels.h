@@ -14,12 +14,16 @@ namespace lsq {
 struct SellDev { int64_t nslices; const int64_t* off; const int32_t* perm; const int32_t* col; const double* val; };
 struct CsrDev {
   int64_t m, n; const int64_t* row_ptr; const int32_t* col; const double* val;
-  SellDev sell;  // used when the product runs with lanes == -2
+  SellDev sell;  // used when the product runs with kernel code -2
 };
 struct CscDev {
   int64_t m, n; const int64_t* col_ptr; const int32_t* row; const double* val;
   SellDev sell;
 };
+// Kernel codes of the two sparse products (ls_info.lanes_csr / lanes_csc and the spmv
+// option): 1, 2, 4, 8, 16, 32 lanes per row; -1 / -3 warp-stream with 16 / 32 rows per
+// warp; -2 sliced ELL.
+inline bool valid_spmv_code(int c) { return (c >= -3 && c <= -1) || c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
 // Scalar slots of the CG state kept on the device (copied to the host each iteration).
 enum {

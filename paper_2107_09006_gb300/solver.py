@@ -22,8 +22,11 @@ class Solver:
 
     Options are the fields of ls_options (tau, nev_max, delta_rel, s_rel, factor_prec
     ('f64' | 'f32' | 'bf16'), maxit, coarse, fixed_iters, eig_maxit, eig_tol,
-    use_graph, time_kernels, equilibrate, variant (0 additive, 1 balanced second level),
-    solver (0 PCG, 1 preconditioned LSQR)).  Arrays may be numpy arrays or tensors; they
+    use_graph, time_kernels, equilibrate, variant (0 additive, 1 balanced second level,
+    2 RAS with the deflated second level), solver (0 PCG, 1 preconditioned LSQR, 2
+    GMRES), restart (GMRES restart length), spmv (0: the sparse-product kernels are
+    chosen by timing at setup; else one kernel code for both products)).  Arrays may be
+    numpy arrays or tensors; they
     are copied by setup.  ``solve`` takes b of shape [m] or [nrhs, m] (up to 32 right-hand
     sides advance together).
     """
