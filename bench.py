@@ -31,7 +31,7 @@ METRIC = "n=1M LS solve s to 1e-8 normal-eq rel resid, mixed vs FP64 form; apply
 # DRAM bytes (read + write) of one k_local_solve launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one pass) on the workload
 # and form named in the key; valid while that kernel and workload stay as they are.
-LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32"): 5.80e9 + 8.57e6}
+LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32"): 5.81e9 + 9.16e6}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--zero-sum", action="store_true",
                     help="nsweep/tausweep on the zero-sum variant of the grid workload (random rows centred to "
                          "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
+    ap.add_argument("--spmv", type=int, default=0,
+                    help="solve mode: force one sparse-product kernel code for A and A^T (0: autotuned)")
     ap.add_argument("--nprob", type=int, default=64)
     ap.add_argument("--nrhs", type=int, default=32)
     return ap.parse_args()
@@ -142,17 +144,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def local_solve_bytes(st: dict, form: str) -> int:
+def local_solve_bytes(st: dict, form: str, restrict: bool = True) -> int:
     """Algorithmic bytes of one local-solve launch: the stored factor tiles (off-diagonal
     panels and inverse diagonal tiles) read by the forward and the backward sweep, the
-    gather of r and the write of y (index, r value, scale, y per local entry), the
-    coarse restriction (Zbar once)."""
+    gather of r and the write of y (index, r value, scale, y per local entry), and the
+    fused coarse restriction (Zbar once) when the launch carries it (the additive
+    operator; the balanced and deflated operators restrict in a kernel of their own)."""
     es = {"f64": 8, "f32": 4, "bf16": 2}[form]
     fac = 2 * st["fac_elems"] * es
     if form == "bf16":
         fac += 2 * (st["fac_elems"] // 1024) * 4
     gather = st["total_local"] * (4 + 8 + 8 + 8)
-    coarse = st["zbar_elems"] * 8
+    coarse = st["zbar_elems"] * 8 if restrict else 0
     return fac + gather + coarse
 
 
@@ -255,7 +258,7 @@ def run_ours(args):
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
                    nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,
-                   solver=solver)
+                   solver=solver, spmv=args.spmv)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()
@@ -283,7 +286,7 @@ def run_ours(args):
         ms_local = sum(i["ms_local"] for i in infos) / max(nl, 1)
         its = sum(i["iters"] for i in infos)
         ms_spmv = sum(i["ms_spmv"] for i in infos) / max(its, 1)
-        lb = local_solve_bytes(st, form)
+        lb = local_solve_bytes(st, form, restrict=variant == 0)
         sb = spmv_bytes(P.m, P.n, P.nnz)
         loc_gbs = lb / (ms_local * 1e-3) / 1e9
         spmv_gbs = sb / (ms_spmv * 1e-3) / 1e9

@@ -453,6 +453,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     if (timed) record_event(h->ev[0], st);
     // beta u = A v - alpha u
     lsq::launch_spmv_csr(csr(h), h->lq_v.p, h->q.p, h->lanes_csr, h->grid_csr, st);
+    if (timed) record_event(h->ev[6], st);
     lsq::launch_axpby(m, 1.0, h->q.p, -alpha, h->lq_u.p, h->lq_u.p, st);
     lsq::launch_dot(m, h->lq_u.p, h->lq_u.p, site(h, lsq::S_TMP, 3), st);
     beta = std::sqrt(dev_sum(h));
@@ -462,6 +463,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     }
     lsq::launch_axpby(m, 1.0 / beta, h->lq_u.p, 0.0, nullptr, h->lq_u.p, st);
     // alpha v = M^{-1} (A^T u - beta q)
+    if (timed) record_event(h->ev[7], st);
     lsq::launch_spmv_csc(csc(h), h->lq_u.p, h->lq_s.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, st);
     if (timed) record_event(h->ev[1], st);
     lsq::launch_axpby(n, 1.0, h->lq_s.p, -beta, h->lq_q.p, h->lq_s.p, st);
@@ -489,12 +491,13 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     be.push_back(beta);
     if (timed) {
       CK(cudaStreamSynchronize(st));
-      float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
-      CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[1]));
+      float ta = 0.f, ta2 = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
+      CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[6]));
+      CK(cudaEventElapsedTime(&ta2, h->ev[7], h->ev[1]));
       CK(cudaEventElapsedTime(&tb, h->ev[2], h->ev[3]));
       CK(cudaEventElapsedTime(&tc, h->ev[3], h->ev[4]));
       CK(cudaEventElapsedTime(&td, h->ev[0], h->ev[5]));
-      inf.ms_spmv += ta; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
+      inf.ms_spmv += ta + ta2; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
     }
     if (fixed > 0) continue;
     if (!checking && phibar * alpha * std::fabs(c) <= 10.0 * rtol * est0) checking = true;
@@ -583,6 +586,7 @@ ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
       double* w = V + (int64_t)(j + 1) * n;
       if (timed) record_event(h->ev[0], st);
       precond(h, vj, zj, 0, false, false, timed);
+      if (timed) record_event(h->ev[6], st);
       apply_C(h, zj, w);
       if (timed) record_event(h->ev[1], st);
       lsq::launch_multi_dot(n, V, n, j + 1, w, h->gm_part.p, h1, st);
@@ -601,7 +605,7 @@ ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
         record_event(h->ev[5], st);
         CK(cudaStreamSynchronize(st));
         float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
-        CK(cudaEventElapsedTime(&ta, h->ev[0], h->ev[1]));
+        CK(cudaEventElapsedTime(&ta, h->ev[6], h->ev[1]));
         CK(cudaEventElapsedTime(&tb, h->ev[2], h->ev[3]));
         CK(cudaEventElapsedTime(&tc, h->ev[3], h->ev[4]));
         CK(cudaEventElapsedTime(&td, h->ev[0], h->ev[5]));

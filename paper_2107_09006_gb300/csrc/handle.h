@@ -172,7 +172,7 @@ struct ls_handle {
   int hist_cap = 0;
 
   cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // kernel timing
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // kernel timing
 
   // independent problems of one batched handle (block-diagonal A): problem q owns rows
   // [m_off[q], m_off[q+1]), columns [n_off[q], n_off[q+1]) and the subdomain ids

@@ -101,4 +101,6 @@ def test_bad_code_rejected(grid96):
     d = grid96
     with pytest.raises(L.LSError) as ex:
         L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=8, spmv=3)
+    with pytest.raises(L.LSError):
+        L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=8, spmv=64)
     assert ex.value.status == L.LS_ERR_INVALID
