@@ -67,3 +67,26 @@ def test_host_index_sets_reject_bad_input(lib):
     assert e.value.status == lib.LS_ERR_INVALID
     with pytest.raises(lib.LSError):
         lib.ls_build_index_sets(P.m, P.n, P.row_ptr, P.col, P.nparts, np.full(P.n, -1, np.int32))
+
+
+@pytest.mark.parametrize("struct", ["ls_options", "ls_info"])
+def test_struct_layout_matches_header(lib, struct, tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's layout: size and
+    the offset of every field (a field added to one side only would shift the rest)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cls = getattr(lib, struct)
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {name}));' for name, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ls_schwarz.h\"\nint main(void) {\n  "
+                   + "\n  ".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, name).offset for name, _ in cls._fields_]
+    assert got == want
