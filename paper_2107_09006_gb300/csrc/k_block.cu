@@ -674,7 +674,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
       }
       __syncthreads();
       TA acc[4] = {0, 0, 0, 0};
-      for (int t = tf[b]; t < b && ok; ++t) {
+      const int tfb = tf[b];  // a register: the barriers in release() would force reloads
+      for (int t = tfb; t < b && ok; ++t) {
         const TF* T = wait_tile();
         tile_colmajor<TF, TA>(T, vring + (size_t)(t % RING) * kT * kT, acc, tile_scale(seq), r0, lane);
         ++seq;
@@ -711,7 +712,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
         if (l < ni && lane < R) a.Y[(o0 + l) * R + lane] = (double)x[u] * a.eqs[o0 + l];
       }
       ok = release();
-      for (int t = b - 1; t >= tf[b] && ok; --t) {
+      const int tfb = tf[b];
+      for (int t = b - 1; t >= tfb && ok; --t) {
         const TF* T = wait_tile();
         TA sdec[4];
         tile_transposed<TF, TA>(T, tin, sdec, tile_scale(seq), r0, lane);
@@ -913,8 +915,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       }
     };
     fetch_rhs(0);
+    // first tile column of the next block row, loaded one block row ahead (in a register:
+    // the barriers of release() would otherwise force a reload on the dependency chain)
+    int tf_next = tf[0];
     // forward sweep
     for (int b = 0; b < nbk && ok; ++b) {
+      const int tfb = tf_next;
+      if (b + 1 < nbk) tf_next = tf[b + 1];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = tid + kThreads * u;
@@ -924,7 +931,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       __syncthreads();
       // panel tiles two at a time (independent products, one barrier per pair)
       float c[4] = {0.f, 0.f, 0.f, 0.f}, c2[4] = {0.f, 0.f, 0.f, 0.f};
-      int t = tf[b];
+      int t = tfb;
       for (; t + 1 < b && ok; t += 2) {
         const float* T1 = wait_tile(0);
         const float* T2 = wait_tile(1);
@@ -962,8 +969,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       }
       ok = release(1);
     }
-    // backward sweep
+    // backward sweep; tf and the equilibration scales of this thread's output rows are
+    // loaded one block row ahead
+    auto fetch_scales = [&](int b, double sc[2]) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = b * kT + mb * 16 + g + 8 * h;
+        sc[h] = l < ni ? a.eqs[o0 + l] : 0.0;
+      }
+    };
+    double sc_next[2];
+    if (nbk > 0) {
+      tf_next = tf[nbk - 1];
+      fetch_scales(nbk - 1, sc_next);
+    }
     for (int b = nbk - 1; b >= 0 && ok; --b) {
+      const int tfb = tf_next;
+      const double scb[2] = {sc_next[0], sc_next[1]};
+      if (b > 0) {
+        tf_next = tf[b - 1];
+        fetch_scales(b - 1, sc_next);
+      }
       // the forward values of tile b - RING, which takes slot b % RING after this step
       float4 refill = make_float4(0.f, 0.f, 0.f, 0.f);
       if (b - RING >= 0) refill = reinterpret_cast<const float4*>(spill + (size_t)(b0 + b - RING) * kT * kT)[tid];
@@ -976,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
         const int l = b * kT + mb * 16 + g + 8 * h;
         const int k = nb * 8 + 2 * t4;
         if (l < ni) {
-          const double sc = a.eqs[o0 + l];
+          const double sc = scb[h];
           if (k < R) a.Y[(o0 + l) * R + k] = (double)x[2 * h] * sc;
           if (k + 1 < R) a.Y[(o0 + l) * R + k + 1] = (double)x[2 * h + 1] * sc;
         }
@@ -997,14 +1023,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
         }
       };
       int t = b - 1;
-      for (; t - 1 >= tf[b] && ok; t -= 2) {
+      for (; t - 1 >= tfb && ok; t -= 2) {
         const float* T1 = wait_tile(0);
         const float* T2 = wait_tile(1);
         update(T1, t);
         update(T2, t - 1);
         ok = release(2);
       }
-      if (ok && t >= tf[b]) {
+      if (ok && t >= tfb) {
         update(wait_tile(0), t);
         ok = release(1);
       }
