@@ -269,7 +269,7 @@ ls_status ls_build_index_sets(int64_t m, int64_t n, const int64_t* row_ptr,
 /* w = A^T (A p) without any allocation by the library.  The paper has no counterpart:
  * this is for callers that cannot call cudaMalloc -- code that records its GPU work
  * into a CUDA graph by stream capture, code whose memory must all come from a
- * framework's own pool, real-time loops that must stay out of the driver's allocator.
+ * framework's own pool, real-time loops that must stay out of the CUDA memory allocator.
  *   m, n, nnz        sizes of A (1 <= m <= 8,388,608; n >= 1)
  *   row_ptr, col, val        A in CSR (device memory: int64[m+1], int32[nnz], f64[nnz])
  *   col_ptr, row, cval       A in CSC (device memory: int64[n+1], int32[nnz], f64[nnz]),

@@ -3,7 +3,7 @@
 // Some callers cannot call cudaMalloc: code that records its GPU work into a CUDA
 // graph by stream capture (allocation calls are not capturable), code that runs inside
 // a framework whose memory must all come from its own pool, and real-time loops that
-// must not enter the driver's allocator.  This entry point lets them apply the
+// must not enter the CUDA memory allocator.  This entry point lets them apply the
 // operator C = A^T A without the library allocating anything: the caller passes A in
 // CSR and CSC form, p and w; the intermediate q = A p lives in a file-scope device
 // array of fixed size, the same array for every call.
