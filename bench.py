@@ -196,6 +196,18 @@ print(json.dumps(dict(n=P.n, N=P.nparts, setup_s=ts, solve_s=times, iters=iters,
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+def solve_config(args, world: int) -> dict:
+    """The benchmark workload, identical in both arms: the grid generator with 4 random rows
+    of 8 entries per grid point plus one 1e-2 identity row per column, so m = 5 n and
+    nnz = 33 n."""
+    n = args.side * args.side
+    N = (-(-args.side // args.block)) ** 2  # square blocks, the last row and column ragged
+    return {"workload": f"grid{args.side}-r3k8-N{N}: n={n}, m={5 * n}, nnz={33 * n}, "
+                        f"{N} subdomains {args.block}x{args.block}, overlap 1, nev_max {args.nev}, tau auto",
+            "rtol": args.rtol, "l2": "inputs larger than L2 (factors alone exceed 129 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -211,7 +223,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1000, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"grid{args.side}-r3k8-N{(args.side // args.block) ** 2}", "rtol": args.rtol},
+            "config": solve_config(args, args.gpus),
+            "form": "oracle: plain FP64 PCG with the two-level preconditioner (CPU, one thread)",
             "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -236,6 +249,8 @@ def run_ours(args):
     t = time.time()
     P = config_scale(side=args.side, block=args.block)
     log(f"[bench] workload generated in {time.time() - t:.1f}s: m={P.m} n={P.n} nnz={P.nnz} N={P.nparts}")
+    if (P.m, P.nnz, P.nparts) != (5 * P.n, 33 * P.n, (-(-args.side // args.block)) ** 2):
+        raise RuntimeError("workload sizes differ from the ones the config line states")
     stream = torch.cuda.current_stream(dev)
     hbm_peak, peak_src = peaks()
     forms = [f for f in args.forms.split(",") if f]
@@ -326,11 +341,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": head["value"] * 1000, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"f32": "f32", "f64": "f64", "bf16": "bf16"}[args.prec], "data": "synthetic",
-        "config": {"workload": f"grid{args.side}-r3k8-N{P.nparts}: n={P.n}, m={P.m}, nnz={P.nnz}, "
-                               f"{P.nparts} subdomains {args.block}x{args.block}, overlap 1, nev_max {args.nev}, tau auto",
-                   "rtol": args.rtol, "form": {"f32": "mixed: FP32 local factors, FP64 flexible CG",
-                                                "f64": "plain FP64", "bf16": "mixed: BF16 local factors"}[args.prec],
-                   "l2": "inputs larger than L2 (factors alone exceed 129 MB)", "parallelism": f"replicas x{world}"},
+        "config": solve_config(args, world),
+        "form": {"f32": "mixed: FP32 local factors, FP64 flexible CG", "f64": "plain FP64",
+                 "bf16": "mixed: BF16 local factors"}[args.prec],
         "roofline": {"bound": "hbm", "achieved": head["local_solve"]["GBps"], "peak": hbm_peak, "unit": "GB/s",
                      "frac": head["local_solve"]["frac"],
                      "traffic": LOCAL_SOLVE_TRAFFIC.get((P.name, args.prec)),
