@@ -104,6 +104,12 @@ typedef struct {
                           row; -1 / -3 warp-stream (16 / 32 rows per warp); -2 sliced
                           ELL (LS_ERR_INVALID else).  ls_info.lanes_csr / lanes_csc
                           report the codes in use.                                    */
+    int test_stall;    /* test hook, 0 (the default) in normal use: 1 makes the
+                          single-vector local-solve kernel issue none of its bulk
+                          copies, so every bounded wait for one gives up (after about
+                          two seconds), the kernel sets the error slot and returns with
+                          nothing in flight, and the solve returns
+                          LS_ERR_DEVICE_TIMEOUT.  The CUDA context stays usable.      */
 } ls_options;
 
 typedef struct {

@@ -28,7 +28,7 @@ class ls_options(ctypes.Structure):
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int),
-                ("restart", ctypes.c_int), ("spmv", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("spmv", ctypes.c_int), ("test_stall", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):

@@ -105,6 +105,7 @@ void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
   a.coarse = with_coarse ? 1 : 0;
   a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
   a.Z = h->Z.p; a.r0 = h->r0.p;
+  a.stall = h->opt.test_stall;
   lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, h->st);
 }
 
@@ -1212,6 +1213,7 @@ void ls_default_options(ls_options* o) {
   o->solver = 0;
   o->restart = 100;
   o->spmv = 0;
+  o->test_stall = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1240,6 +1242,7 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
       throw LsError(LS_ERR_INVALID, "the deflated RAS variant is not symmetric: it needs solver = 2 (GMRES)");
     if (h->opt.solver == 2 && (h->opt.restart < 1 || h->opt.restart > 1000))
       throw LsError(LS_ERR_INVALID, "restart must lie in [1, 1000]");
+    if (h->opt.test_stall != 0 && h->opt.test_stall != 1) throw LsError(LS_ERR_INVALID, "test_stall must be 0 or 1");
     if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))
       throw LsError(LS_ERR_INVALID, "spmv must be 0 or a sparse-product kernel code");
     if (h->opt.variant != 0 && nprob > 1)

@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     prod.next();
     ++issued;
   };
-  if (issuer) {
+  // (a.stall, a test hook: no copy is issued, every wait below runs out after its bound
+  // and the CTA takes the error path with nothing in flight)
+  if (issuer && !a.stall) {
     prod.start(tf, nb, CC);
     for (int s = 0; s < S - 1 && !prod.done(); ++s) issue(s);
   }
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   int q = 0;
   while (!cons.done()) {
     const int stage = q % S;
-    if (issuer && !prod.done()) issue((q + S - 1) % S);
+    if (issuer && !a.stall && !prod.done()) issue((q + S - 1) % S);
     {
       const uint32_t parity = (uint32_t)((q / S) & 1);
       if (!mbar_try_wait(&bars[stage], parity)) {

@@ -131,6 +131,7 @@ struct LocalArgs {
   int coarse; const int64_t* int_off; const int32_t* int_glob; const int64_t* zoff;
   const int32_t* coff; const double* Z; double* r0;
   double* err;  // set to 1 when a bounded wait on a copy gives up
+  int stall;    // test hook: 1 issues no copies, so the bounded waits run out
 };
 size_t local_solve_smem(int prec, int max_nb);
 void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
