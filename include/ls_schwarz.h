@@ -105,10 +105,10 @@ typedef struct {
                           ELL (LS_ERR_INVALID else).  ls_info.lanes_csr / lanes_csc
                           report the codes in use.                                    */
     int test_stall;    /* test hook, 0 (the default) in normal use: 1 makes the
-                          single-vector local-solve kernel issue none of its bulk
-                          copies, so every bounded wait for one gives up (after about
-                          two seconds), the kernel sets the error slot and returns with
-                          nothing in flight, and the solve returns
+                          local-solve kernels (single-vector and block) issue none of
+                          their bulk copies, so every bounded wait for one gives up
+                          (after about two seconds), the kernel sets the error slot and
+                          returns with nothing in flight, and the solve returns
                           LS_ERR_DEVICE_TIMEOUT.  The CUDA context stays usable.      */
 } ls_options;
 

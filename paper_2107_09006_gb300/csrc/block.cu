@@ -78,6 +78,7 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   a.tsc = h->prec == LS_PREC_BF16 ? h->tsc.p : nullptr;
   a.Rv = Rin; a.Y = B.Y.p; a.R = R; a.Vg = B.Vg.p; a.ring = B.ring;
   a.err = h->scal.p + lsq::S_ERR;
+  a.stall = h->opt.test_stall;
   if (B.use_tc) {
     a.fac = B.Lsw.p;
     a.tsc = nullptr;

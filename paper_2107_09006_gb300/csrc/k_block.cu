@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
       ++pnext;
       ++issued;
     };
-    if (tid == 0)
+    if (tid == 0 && !a.stall)  // (a.stall, a test hook: no copies, so every wait runs out)
       while (pnext < 2 * ntile && issued < q + S) issue();
     auto wait_tile = [&]() -> const TF* {
       const int stage = (int)(q % S);
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
       __syncthreads();
       if (sh[1]) return false;
       ++q;
-      if (tid == 0 && pnext < 2 * ntile) issue();
+      if (tid == 0 && !a.stall && pnext < 2 * ntile) issue();
       return true;
     };
     auto tile_scale = [&](uint32_t seq) -> TA {
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       ++pnext;
       ++issued;
     };
-    if (tid == 0)
+    if (tid == 0 && !a.stall)  // (a.stall, a test hook: no copies, so every wait runs out)
       while (pnext < 2 * ntile && issued < q + S) issue();
     // tile q + off of the sequence (off = 0, 1; both are in flight: S >= 2)
     auto wait_tile = [&](uint32_t off) -> const float* {
@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
       __syncthreads();
       if (sh[1]) return false;
       q += used;
-      if (tid == 0)
+      if (tid == 0 && !a.stall)
         while (pnext < 2 * ntile && issued < q + S) issue();
       return true;
     };

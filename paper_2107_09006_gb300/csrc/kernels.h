@@ -210,6 +210,7 @@ struct BLocalArgs {
   void* Vg;  // forward-sweep spill: 32 x 32 arithmetic-precision tile per block row
   int ring;  // tiles of the solution window kept in shared memory (>= widest block row)
   double* err;
+  int stall;  // test hook: 1 issues no copies, so the bounded waits run out
 };
 size_t block_local_smem(int fac_bytes, int arith_bytes, int ring);
 int block_local_occupancy(int prec, int ring);

@@ -6,7 +6,8 @@ skips the rest of its work and returns with no copy in flight, and the host turn
 slot into LS_ERR_DEVICE_TIMEOUT.  The option `test_stall` makes the kernel issue none of
 its copies, so every wait runs out: the solve must fail with that status within a few
 seconds, and the CUDA context must stay usable (a handle without the hook then solves
-to 1e-10 against the oracle).
+to 1e-10 against the oracle).  The same holds for both block (multi right-hand-side)
+local-solve kernels.
 """
 import time
 
@@ -41,6 +42,27 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     A = O.schwarz.as_csr(P.m, P.n, P.row_ptr, P.col, P.val)
     xo, _ = O.pcg(A, P.b, O.build_two_level(A, P.part, P.nparts, tau=0.0, nev_max=16).apply, rtol=1e-12)
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+    S2.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_block_path_bounded_wait_reports_timeout(prec):
+    """The same on the multi right-hand-side path: the tensor-core kernel (FP32 factors)
+    and the CUDA-core kernel (FP64 factors)."""
+    P = config_tiny()
+    B = np.stack([P.b, np.random.default_rng(3).standard_normal(P.m)])
+    S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec, test_stall=1)
+    t0 = time.time()
+    with pytest.raises(L.LSError) as ex:
+        S.solve(B, rtol=1e-8)
+    assert ex.value.status == L.LS_ERR_DEVICE_TIMEOUT
+    assert time.time() - t0 < 60.0
+    S.close()
+    torch.cuda.synchronize()
+    S2 = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec)
+    X, _ = S2.solve(B, rtol=1e-10)
+    its, rel = S2.batch_stats(2)
+    assert (rel <= 1e-10).all()
     S2.close()
 
 
