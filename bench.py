@@ -31,7 +31,7 @@ METRIC = "n=1M LS solve s to 1e-8 normal-eq rel resid, mixed vs FP64 form; apply
 # DRAM bytes (read + write) of one k_local_solve launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one pass) on the workload
 # and form named in the key; valid while that kernel and workload stay as they are.
-LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32"): 5.81e9 + 9.16e6}
+LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32"): 5.81e9 + 9.02e6}
 FALLBACK_HBM_GBS = 6800.0
 
 
