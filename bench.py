@@ -7,7 +7,8 @@ nonzeros inside Chebyshev radius 3 of a random centre (N(0,1) values) plus 1e-2 
 256 subdomains of 64 x 64 columns, overlap 1, at most 32 coarse vectors each (tau
 automatic).  A step is one complete ls_solve (x_0 = 0 to ||A^T(b - Ax)|| <= 1e-8 ||A^T b||);
 setup is timed separately.  The headline form is the mixed one (FP32 local factors
-inside an FP64 flexible CG); the plain FP64 form runs on the same problem beside it.
+inside an FP64 flexible CG); the plain FP64 form and GMRES with RAS + the deflated
+second level run on the same problem beside it (`--forms`).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
