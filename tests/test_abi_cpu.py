@@ -91,3 +91,23 @@ def test_struct_layout_matches_header(lib, struct, tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(cls)] + [getattr(cls, name).offset for name, _ in cls._fields_]
     assert got == want
+
+
+def test_enum_values_match_header(lib, tmp_path):
+    """Every status, precision and query constant of the binding has the value the C
+    compiler gives the header's enumerator of the same name."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    hdr = open(os.path.join(ROOT, "include", "ls_schwarz.h")).read()
+    names = sorted(set(re.findall(r"^\s*(LS_(?:OK|ERR_\w+|PREC_\w+|Q_\w+))\s*=", hdr, re.M)))
+    assert len(names) >= 20
+    src = tmp_path / "enums.c"
+    src.write_text("#include <stdio.h>\n#include \"ls_schwarz.h\"\nint main(void) {\n"
+                   + "".join(f'  printf("%d\\n", (int){n});\n' for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "enums"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == [getattr(lib, n) for n in names]
