@@ -9,9 +9,9 @@ It follows Al Daas, Jolivet & Scott, "A robust algebraic domain decomposition
 preconditioner for sparse normal equations" (arXiv 2107.09006):
 
 * index sets Xi_i, Omega_Gamma_i, Omega_i              (Section 3, eq. (3.1))
-* partition of unity D_i                                (Section 3.4.1)
+* partition of unity D_i                                (Section 3.3.1)
 * local matrices C_ii and splittings C~_ii              (Section 3.1, eq. (3.2))
-* shifted generalized eigenproblems, threshold tau      (Section 3.4.2, eqs. (3.3)-(3.6))
+* shifted generalized eigenproblems, threshold tau      (Section 3.3.2, eqs. (3.3)-(3.6))
 * coarse space R_0 and C_00                             (Lemma 2.5, Algorithm 1)
 * two-level additive preconditioner                     (eq. (2.3))
 * PCG on C x = A^T b with C applied as A^T (A .)        (Section 4.1.3)
@@ -40,6 +40,7 @@ from .schwarz import (  # noqa: F401
     fgmres,
     adjoint_gradient,
     multiplicity_km,
+    subdomain_colouring,
     colouring_kc,
     theorem26_bound,
 )

@@ -67,7 +67,7 @@ def restriction(Om_i: np.ndarray, n: int) -> np.ndarray:
 
 
 def partition_of_unity(nI: int, ni: int) -> np.ndarray:
-    """D_i: ones on the n_I,i interior positions, zeros on Omega_Gamma,i (Section 3.4.1)."""
+    """D_i: ones on the n_I,i interior positions, zeros on Omega_Gamma,i (Section 3.3.1)."""
     d = np.zeros(ni)
     d[:nI] = 1.0
     return d
@@ -645,9 +645,12 @@ def multiplicity_km(A: sp.csr_matrix, S: IndexSets) -> int:
     return int(cnt.max()) if cnt.size else 0
 
 
-def colouring_kc(A: sp.csr_matrix, S: IndexSets) -> int:
-    """Upper bound on k_c (Lemma 2.2): greedy colouring of the subdomain graph where
-    i ~ j iff C(Omega_i, Omega_j) has a structural nonzero."""
+def subdomain_colouring(A: sp.csr_matrix, S: IndexSets) -> list:
+    """Greedy colouring of the subdomain graph of Lemma 2.2: i ~ j iff C(Omega_i, Omega_j)
+    has a structural nonzero, so that subdomains of one colour span mutually
+    C-orthogonal spaces.  Subdomains are visited in index order and each takes the
+    smallest colour none of its coloured neighbours has.  Returns one colour per
+    subdomain (0-based)."""
     C = (abs(A).T @ abs(A)).tocsr()
     N = S.N
     n = A.shape[1]
@@ -669,7 +672,15 @@ def colouring_kc(A: sp.csr_matrix, S: IndexSets) -> int:
         while c in used:
             c += 1
         colour[i] = c
-    return max(colour) + 1 if N else 0
+    return colour
+
+
+def colouring_kc(A: sp.csr_matrix, S: IndexSets) -> int:
+    """Upper bound on k_c of Lemma 2.2 (the fewest colours such that same-coloured
+    subdomains are mutually C-orthogonal): the number of colours of the greedy
+    colouring above."""
+    colour = subdomain_colouring(A, S)
+    return max(colour) + 1 if colour else 0
 
 
 def theorem26_bound(kc: int, km: int, tau: float, variant: str = "thm") -> float:

@@ -403,3 +403,168 @@ def test_adjoint_gradient_finite_differences():
         bm[k] -= h
         fd = (loss(v, bp) - loss(v, bm)) / (2 * h)
         assert abs(fd - gb[k]) <= 1e-6 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------- shifts (Section 4.1.2)
+def _hand():
+    return json.load(open(os.path.join(GOLD, "paper_example.json")))["hand_derived"]
+
+
+def test_global_shift_worked_example():
+    """delta = 1e-10 ||C||_F with C = A^T A (Section 4.1.2), against ||C||_F^2 = 18592 worked
+    out by hand from the printed 5x4 A; delta enters every C_ii (dense and banded modes)
+    and nothing else.  ||A||_F (204), the spectral norm of C or a missing square root
+    would all fail here."""
+    h = _hand()
+    Ad, A, part = _example()
+    assert np.array_equal(Ad.T @ Ad, np.array(h["C"], float))
+    assert float(np.sum(np.array(h["C"], float) ** 2)) == h["C_frob_sq"]
+    want = 1e-10 * np.sqrt(h["C_frob_sq"])
+    assert abs(O.global_shift(A, 1e-10) / want - 1) < 1e-15
+    assert abs(O.global_shift(A, 0.25) / (0.25 * np.sqrt(h["C_frob_sq"])) - 1) < 1e-15
+    M = O.build_two_level(A, part, 2, tau=0.6, nev_max=300)
+    assert abs(M.delta / want - 1) < 1e-15
+    S = O.index_sets(A, part, 2)
+    from oracle.schwarz import _local_banded
+    for i, (kc, kt) in enumerate([("C11", "Ct11"), ("C22", "Ct22")]):
+        Cii, Ct = O.local_matrices(A, S, i, want)
+        assert np.allclose(Cii, np.array(h[kc], float) + want * np.eye(3), rtol=0, atol=1e-14)
+        assert np.array_equal(Ct, np.array(h[kt], float))  # the splitting carries no delta
+        srt, Cb, Ctb, s, _, _ = _local_banded(A, S, i, want, 1e-8)
+        perm = [list(S.Om[i]).index(j) for j in srt]  # banded mode: ascending global order
+        assert np.allclose(Cb.toarray(), (np.array(h[kc], float) + want * np.eye(3))[np.ix_(perm, perm)],
+                           rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("s_rel", [1e-8, 1e-1])
+def test_gevp_shift_worked_example(s_rel):
+    """The GEVP shift s_i = s_rel ||C~_ii||_F (Section 4.1.2) with ||C~_11||_F^2 = 1948 and
+    ||C~_22||_F^2 = 17044 worked out by hand: the oracle's eigenvalues of
+    D C_ii D v = lambda (C~_ii + s_i I) v equal the roots of the exact characteristic
+    polynomial of that pencil (sympy, 40 digits).  At s_rel = 0.1 a shift taken with
+    another norm would move the eigenvalues by percent; at the paper's 1e-8 by about
+    1e-9 relative, still far above the 1e-12 tolerance.  The banded mode computes the
+    same s."""
+    sympy = pytest.importorskip("sympy")
+    h = _hand()
+    _, A, part = _example()
+    S = O.index_sets(A, part, 2)
+    from oracle.schwarz import _local_banded
+    lam_sym = sympy.Symbol("lam")
+    for i, (kc, kt, kf) in enumerate([("C11", "Ct11", "Ct11_frob_sq"), ("C22", "Ct22", "Ct22_frob_sq")]):
+        assert int(np.sum(np.array(h[kt]) ** 2)) == h[kf]
+        s = sympy.Float(s_rel, 40) * sympy.sqrt(h[kf])
+        d = sympy.diag(1, 1, 0)
+        DCD = d * sympy.Matrix(h[kc]) * d
+        B = sympy.Matrix(h[kt]) + s * sympy.eye(3)
+        poly = sympy.Poly((DCD - lam_sym * B).det(), lam_sym)
+        exact = sorted((float(sympy.re(r)) for r in poly.nroots(n=40)), reverse=True)
+        exact = exact + [0.0] * (3 - len(exact))
+        Cii, Ct = O.local_matrices(A, S, i, 0.0)
+        lam, _ = O.gevp_local(Cii, Ct, 2, s_rel=s_rel)
+        top = max(abs(x) for x in exact)
+        assert np.allclose(lam, exact, rtol=1e-12, atol=1e-12 * top), (lam, exact)
+        _, _, _, sb, _, _ = _local_banded(A, S, i, 0.0, s_rel)
+        assert abs(sb / float(s) - 1) < 1e-14
+
+
+def test_select_coarse_kappa_branch():
+    """Eq. (3.6): keep lambda > 1/tau, or lambda >= 1/(kappa(C_ii) eps) when that bound is
+    the smaller one, largest first and at most nev_max (hand-made spectrum)."""
+    lam = np.array([10.0, 5.0, 3.0, 2.0, 0.5])
+    V = np.eye(5)
+    Z, kept = O.select_coarse(lam, V, 5, tau=0.1, nev_max=10)  # 1/tau = 10: strict, nothing kept
+    assert kept.size == 0 and Z.shape == (5, 0)
+    kappa = 1.0 / (3.0 * np.finfo(float).eps)  # 1/(kappa eps) = 3 < 10
+    Z, kept = O.select_coarse(lam, V, 5, tau=0.1, nev_max=10, kappa_cii=kappa)
+    assert kept.tolist() == [10.0, 5.0, 3.0] and np.array_equal(Z, V[:, :3])
+    Z, kept = O.select_coarse(lam, V, 3, tau=0.1, nev_max=2, kappa_cii=kappa)
+    assert kept.tolist() == [10.0, 5.0] and Z.shape == (3, 2)
+    Z, kept = O.select_coarse(lam, V, 5, tau=1 / 2.5, nev_max=10, kappa_cii=1.0)  # bound 1/eps: unused
+    assert kept.tolist() == [10.0, 5.0, 3.0]
+
+
+# --------------------------------------------------------------------------- k_c (Lemma 2.2)
+def _subdomain_graph_dense(A, S):
+    """i ~ j iff the structural C = |A|^T |A| couples Omega_i and Omega_j (dense check)."""
+    B = (A.toarray() != 0).astype(float)
+    C = B.T @ B
+    return C, [[j for j in range(S.N) if j != i and C[np.ix_(S.Om[i], S.Om[j])].any()] for i in range(S.N)]
+
+
+def _chromatic_number(adj):
+    """Fewest colours of a proper colouring, by backtracking (tiny graphs only)."""
+    N = len(adj)
+    for k in range(1, N + 1):
+        col = [-1] * N
+
+        def place(i):
+            if i == N:
+                return True
+            for c in range(k):
+                if all(col[j] != c for j in adj[i] if j < i):
+                    col[i] = c
+                    if place(i + 1):
+                        return True
+            col[i] = -1
+            return False
+
+        if place(0):
+            return k
+    return 0
+
+
+@pytest.mark.parametrize("case", ["tiny", "blocks12_r1", "blocks12_r2"])
+def test_colouring_proper_and_minimal(case, tiny):
+    """k_c of Lemma 2.2: the oracle's colouring is proper (same-coloured subdomains are
+    mutually C-orthogonal, checked on the dense C), so its count bounds k_c from above,
+    and here it equals the brute-force chromatic number, so the Theorem 2.6 checks that
+    use it are not loosened by an over-count."""
+    if case == "tiny":
+        A = as_csr(tiny.m, tiny.n, tiny.row_ptr, tiny.col, tiny.val)
+        part, N = tiny.part, tiny.nparts
+    else:
+        r, k = (1, 3) if case == "blocks12_r1" else (2, 4)
+        m, n, rp, c, v, _, _ = make_grid_ls(12, 12, 2, k, r, 3)
+        A = as_csr(m, n, rp, c, v)
+        part, N = block_partition(12, 12, 4, 4), 9
+    S = O.index_sets(A, part, N)
+    colour = O.subdomain_colouring(A, S)
+    C, adj = _subdomain_graph_dense(A, S)
+    for i in range(N):
+        for j in range(i + 1, N):
+            if colour[i] == colour[j]:
+                assert not C[np.ix_(S.Om[i], S.Om[j])].any(), (i, j)
+    kc = O.colouring_kc(A, S)
+    assert kc == max(colour) + 1 == _chromatic_number(adj)
+
+
+@pytest.mark.parametrize("s,kc_hand", [(2, 3), (3, 2), (4, 2)])
+def test_colouring_chain_by_hand(s, kc_hand):
+    """A 1-D chain (row r couples columns r and r+1, plus identity rows): C is tridiagonal
+    and Omega_i is strip i widened by one column on each side.  Strips of s >= 3 columns
+    then touch only their neighbours (a path: two colours); strips of 2 columns also
+    touch the strip after next (three colours)."""
+    n = 12
+    Ad = np.zeros((2 * n - 1, n))
+    for r in range(n - 1):
+        Ad[r, r], Ad[r, r + 1] = 1.0, 1.0 + 0.5 * r
+    Ad[n - 1 + np.arange(n), np.arange(n)] = 1e-2
+    rp, c, v = csr_from_dense(Ad)
+    A = as_csr(2 * n - 1, n, rp, c, v)
+    part = (np.arange(n) // s).astype(np.int32)
+    N = int(part.max()) + 1
+    S = O.index_sets(A, part, N)
+    for i in range(N):
+        lo, hi = max(0, s * i - 1), min(n - 1, s * i + s)
+        assert sorted(S.Om[i].tolist()) == list(range(lo, hi + 1))
+    assert O.colouring_kc(A, S) == kc_hand
+
+
+def test_theorem26_bound_hand_values():
+    """Theorem 2.6's bound (k_c + 1)(2 + (2 k_c + 1) k_m / tau) and its Section 3.2
+    restatement (k_c + 1)(2 + 2 (k_c + 1) k_m / tau), evaluated by hand at k_c = 4,
+    k_m = 3, tau = 1/2: 5 (2 + 54) = 280 and 5 (2 + 60) = 310."""
+    assert O.theorem26_bound(4, 3, 0.5) == 280.0
+    assert O.theorem26_bound(4, 3, 0.5, "sec32") == 310.0
+    assert O.theorem26_bound(0, 1, 1.0) == 3.0  # one colour: 1 (2 + 1)
