@@ -273,9 +273,10 @@ ls_status ls_build_index_sets(int64_t m, int64_t n, const int64_t* row_ptr,
 /* ---- allocation-free entry point ------------------------------------------------ */
 
 /* w = A^T (A p) without any allocation by the library.  The paper has no counterpart:
- * this is for callers that cannot call cudaMalloc -- code that records its GPU work
- * into a CUDA graph by stream capture, code whose memory must all come from a
- * framework's own pool, real-time loops that must stay out of the CUDA memory allocator.
+ * this is for callers that cannot call cudaMalloc -- code whose device memory must all
+ * come from a framework's own pool or from a fixed budget set aside at start-up, and
+ * real-time loops that must stay out of the CUDA memory allocator (cudaMalloc and
+ * cudaFree can synchronise the device and take an unbounded time).
  *   m, n, nnz        sizes of A (1 <= m <= 8,388,608; n >= 1)
  *   row_ptr, col, val        A in CSR (device memory: int64[m+1], int32[nnz], f64[nnz])
  *   col_ptr, row, cval       A in CSC (device memory: int64[n+1], int32[nnz], f64[nnz]),
@@ -283,13 +284,21 @@ ls_status ls_build_index_sets(int64_t m, int64_t n, const int64_t* row_ptr,
  *   p (f64[n], device)       input;  w (f64[n], device) output
  *   stream                   cudaStream_t to launch on (NULL: the legacy default stream)
  * The intermediate q = A p lives in one fixed file-scope device array of 8,388,608
- * doubles (64 MB) per GPU, held from the first call on that GPU until the process
- * exits; larger m returns LS_ERR_INVALID.  The first call on a device looks up the
- * array's device address (once per device, with that device current): make that first
- * call before any stream capture.  All calls share the array: calls whose work can
- * overlap on the GPU (other streams, other threads) race and must be ordered by the
- * caller.  The call is asynchronous on `stream`; the inputs are not validated beyond
- * sizes and NULL pointers.  Messages: ls_noalloc_last_error(). */
+ * doubles (64 MB) per GPU; larger m returns LS_ERR_INVALID.  The array belongs to this
+ * library's module for that source file and is reserved when the module loads into a
+ * CUDA context: at the first call on that device under lazy module loading (the CUDA
+ * default), at context creation under CUDA_MODULE_LOADING=EAGER, for every process
+ * that loads the library; it is held until the context is destroyed or the process
+ * exits.  The first call in a context looks up the array's device address (once per
+ * device and context, with that device current; a context made after cudaDeviceReset
+ * gets its own lookup): make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls whose work can overlap
+ * on the GPU (other streams, other threads) race and must be ordered by the caller.
+ * The call is asynchronous on `stream`; the library checks only sizes and NULL
+ * pointers (the Python binding also checks dtypes, lengths and devices); a pointer of
+ * the wrong kind or length is read or written out of bounds on the device.  Errors:
+ * LS_ERR_INVALID, LS_ERR_CUDA (also when an error from earlier work is already pending
+ * on this thread: it is reported, not cleared).  Messages: ls_noalloc_last_error(). */
 ls_status ls_normal_product_noalloc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
                                     const double* val, const int64_t* col_ptr, const int32_t* row,
                                     const double* cval, int64_t nnz, const double* p, double* w,

@@ -192,9 +192,42 @@ def ls_query(h, kind, i, out):
     return out
 
 
+def _check_noalloc_args(m, n, nnz, row_ptr, col, val, col_ptr, row, cval, p, w, require_cuda=True):
+    """The C call checks only sizes and NULL pointers and launches its kernels on the raw
+    addresses, so a host array, a wrong dtype or a short array would be read or written
+    out of bounds on the device.  Every array must be a contiguous torch tensor of the
+    exact dtype and length below, all on the current CUDA device; ValueError otherwise."""
+    import torch
+    m, n, nnz = int(m), int(n), int(nnz)
+    spec = (("row_ptr", row_ptr, torch.int64, m + 1), ("col", col, torch.int32, nnz),
+            ("val", val, torch.float64, nnz), ("col_ptr", col_ptr, torch.int64, n + 1),
+            ("row", row, torch.int32, nnz), ("cval", cval, torch.float64, nnz),
+            ("p", p, torch.float64, n), ("w", w, torch.float64, n))
+    for name, t, dt, length in spec:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name}: a torch tensor is required, got {type(t).__name__}")
+        if t.dtype != dt:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected {dt}")
+        if t.dim() != 1 or t.numel() != length:
+            raise ValueError(f"{name}: shape {tuple(t.shape)}, expected ({length},)")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+    if require_cuda:
+        cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+        for name, t, _, _ in spec:
+            if t.device.type != "cuda" or t.device.index != cur:
+                raise ValueError(f"{name}: on {t.device}, expected the current CUDA device (cuda:{cur})")
+
+
 def ls_normal_product_noalloc(m, n, row_ptr, col, val, col_ptr, row, cval, nnz, p, w, stream=None):
-    """w = A^T (A p) with no allocation by the library (device arrays in, device w out);
-    asynchronous on ``stream`` (a raw cudaStream_t handle or None)."""
+    """w = A^T (A p) with no allocation by the library, for callers that cannot call
+    cudaMalloc (device memory owned by a framework pool or a fixed budget, real-time
+    loops).  Every array is a contiguous CUDA tensor on the current device: row_ptr
+    int64[m+1], col int32[nnz], val float64[nnz] (CSR), col_ptr int64[n+1], row
+    int32[nnz], cval float64[nnz] (CSC), p and w float64[n]; anything else raises
+    ValueError before the call.  Asynchronous on ``stream`` (a raw cudaStream_t handle
+    or None)."""
+    _check_noalloc_args(m, n, nnz, row_ptr, col, val, col_ptr, row, cval, p, w)
     st = _lib.ls_normal_product_noalloc(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(col_ptr),
                                         _ptr(row), _ptr(cval), int(nnz), _ptr(p), _ptr(w), stream)
     if st != LS_OK:

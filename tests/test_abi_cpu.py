@@ -111,3 +111,35 @@ def test_enum_values_match_header(lib, tmp_path):
     subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == [getattr(lib, n) for n in names]
+
+
+def test_noalloc_binding_rejects_bad_arguments(lib):
+    """The allocation-free product's binding refuses, before any C call, what the C side
+    would launch kernels on blindly: non-tensors, wrong dtypes, wrong lengths, and
+    tensors that are not on the current CUDA device."""
+    torch = pytest.importorskip("torch")
+    m, n, nnz = 7, 4, 10
+    good = dict(row_ptr=torch.zeros(m + 1, dtype=torch.int64), col=torch.zeros(nnz, dtype=torch.int32),
+                val=torch.zeros(nnz, dtype=torch.float64), col_ptr=torch.zeros(n + 1, dtype=torch.int64),
+                row=torch.zeros(nnz, dtype=torch.int32), cval=torch.zeros(nnz, dtype=torch.float64),
+                p=torch.zeros(n, dtype=torch.float64), w=torch.zeros(n, dtype=torch.float64))
+    order = ("row_ptr", "col", "val", "col_ptr", "row", "cval", "p", "w")
+
+    def check(require_cuda=False, **over):
+        a = dict(good, **over)
+        lib._check_noalloc_args(m, n, nnz, *(a[k] for k in order), require_cuda=require_cuda)
+
+    check()  # the host-side shape and dtype checks pass on well-formed arguments
+    bad = {"row_ptr": torch.zeros(m + 1, dtype=torch.int32), "col": torch.zeros(nnz, dtype=torch.int64),
+           "val": torch.zeros(nnz, dtype=torch.float32), "cval": torch.zeros(nnz + 1, dtype=torch.float64),
+           "row": torch.zeros(nnz - 1, dtype=torch.int32), "col_ptr": torch.zeros(n, dtype=torch.int64),
+           "p": torch.zeros(n + 1, dtype=torch.float64), "w": np.zeros(n)}
+    for k, v in bad.items():
+        with pytest.raises(ValueError, match=k):
+            check(**{k: v})
+    with pytest.raises(ValueError, match="row_ptr"):
+        check(row_ptr=torch.zeros(2 * (m + 1), dtype=torch.int64)[::2])  # strided view
+    with pytest.raises(ValueError, match="CUDA device"):
+        check(require_cuda=True)  # host tensors
+    with pytest.raises(ValueError):
+        lib.ls_normal_product_noalloc(m, n, *(good[k] for k in order[:6]), nnz, good["p"], good["w"])
