@@ -60,9 +60,6 @@ typedef enum {
 } ls_precision;
 
 typedef struct {
-    double tau;        /* eigenvalue threshold: keep lambda > 1/tau (Lemma 2.4).  tau <= 0
-                          selects it automatically: 1/tau = max_i lambda_{i, nev_max+1},
-                          so no subdomain keeps more than nev_max vectors.             */
     int nev_max;       /* most coarse vectors per subdomain (Section 4 uses 300)       */
     double delta_rel;  /* construction shift delta = delta_rel ||C||_F (Section 4.1.2) */
     double s_rel;      /* GEVP shift s_i = s_rel ||C~_ii||_F (Section 4.1.2)           */
@@ -138,32 +135,40 @@ typedef struct {
 
 typedef struct ls_handle ls_handle;
 
-/* Fill *opt with the defaults: tau = 0 (auto), nev_max = 16, delta_rel = 1e-10,
+/* Fill *opt with the defaults: nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
  * equilibrate = 0, variant = 0, solver = 0, restart = 100. */
 void ls_default_options(ls_options* opt);
 
-/* Build the preconditioner (Algorithm 1) for A given as CSR and a nonoverlapping
- * column partition.
+/* Build the preconditioner (Algorithm 1, whose inputs are A, the subdomain count N and
+ * the threshold tau) for A given as CSR and a nonoverlapping column partition.
  *   m, n            rows and columns of A (m >= 1, n >= 1)
  *   row_ptr[m+1]    int64 CSR row offsets; col[nnz] int32; val[nnz] float64
  *   nparts          number N of subdomains (1 <= N <= n)
  *   part[n]         int32 subdomain id of every column (the sets Omega_I,i)
  *   overlap         must be 1 (Omega_Gamma,i = distance one in G(C), Section 2);
  *                   any other value returns LS_ERR_UNSUPPORTED
+ *   tau             eigenvalue threshold of the coarse space: keep lambda > 1/tau
+ *                   (Lemma 2.4, eq. (3.6)), at most opt->nev_max vectors per subdomain,
+ *                   largest first.  tau <= 0 selects it automatically:
+ *                   1/tau = max_i lambda_{i, nev_max+1}, so no subdomain keeps more than
+ *                   nev_max vectors and the cap never truncates.  tau >= 1 returns
+ *                   LS_ERR_UNSUPPORTED (it would keep the eigenvalue-1 cluster).
  *   opt             options (NULL: defaults)
- *   stream          cudaStream_t the handle uses (NULL: the handle creates its own)
+ *   stream          cudaStream_t the handle runs its work on (NULL: the handle creates
+ *                   its own non-blocking stream); setup is ordered after the work
+ *                   already queued on it and has finished when the call returns
  *   out             receives the handle
  * The index sets are built on the host; local matrices, their Cholesky factors,
  * the eigensolves and the coarse operator are built on the device.  A and the
  * partition are copied: the caller may free them afterwards.
  * Errors: LS_ERR_INVALID (sizes, unsorted or out-of-range indices, part out of
  * range, non-finite values), LS_ERR_FACTOR (info via ls_handle_info), LS_ERR_EIGEN,
- * LS_ERR_OOM, LS_ERR_CUDA. */
+ * LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_UNSUPPORTED. */
 ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
                    const double* val, int32_t nparts, const int32_t* part, int overlap,
-                   const ls_options* opt, void* stream, ls_handle** out);
+                   double tau, const ls_options* opt, void* stream, ls_handle** out);
 
 /* Batched setup: nprob independent least-squares problems in one handle, given as one
  * block-diagonal matrix (the "many problems share a launch" pattern).
@@ -174,12 +179,13 @@ ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* 
  *   part[n]         subdomain ids; the ids of problem q form one range, in problem
  *                   order (problem 0 owns ids 0 .. N_1-1, problem 1 the next ones, ...)
  * Every problem is set up as if alone: its own delta = delta_rel ||C_q||_F, its own
- * automatic threshold (tau <= 0) and its own dense coarse block.  Other arguments and
- * errors as ls_setup (LS_ERR_INVALID also for a row or subdomain crossing problems). */
+ * automatic threshold (tau <= 0; tau > 0 applies to every problem) and its own dense
+ * coarse block.  Other arguments and errors as ls_setup (LS_ERR_INVALID also for a row
+ * or subdomain crossing problems). */
 ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
                            const int64_t* row_ptr, const int32_t* col, const double* val,
-                           int32_t nparts, const int32_t* part, int overlap, const ls_options* opt,
-                           void* stream, ls_handle** out);
+                           int32_t nparts, const int32_t* part, int overlap, double tau,
+                           const ls_options* opt, void* stream, ls_handle** out);
 
 /* Solve min ||A x - b|| for nrhs right-hand sides by PCG on C x = A^T b with x_0 = 0.
  *   b[m * nrhs]     column-major right-hand sides (host or device)
@@ -188,6 +194,13 @@ ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n
  *                   the true one fails, CG restarts from it)
  *   x[n * nrhs]     output, column-major (host or device)
  *   info            statistics (may be NULL)
+ *   stream          the caller's cudaStream_t (NULL: the legacy default stream, as in
+ *                   every CUDA API).  The call's device work starts after the work
+ *                   already queued on `stream`, and work queued on `stream` after the
+ *                   call is ordered after it.  The work itself runs on the handle's
+ *                   stream (fixed at ls_setup: its CUDA graphs are captured there);
+ *                   passing that stream adds nothing, another one adds an event
+ *                   record and wait at entry and at exit.
  * One right-hand side on a single-problem handle runs the single-vector path.
  * Otherwise (nrhs in 1..32, or a batched handle) all right-hand sides and problems
  * advance together: every kernel of an iteration serves all of them, each (problem,
@@ -197,7 +210,7 @@ ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n
  * Errors: LS_ERR_NOT_CONVERGED (x holds the last iterate), LS_ERR_NONFINITE,
  * LS_ERR_UNSUPPORTED (nrhs > 32 on the multi right-hand-side path). */
 ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x,
-                   ls_info* info);
+                   ls_info* info, void* stream);
 
 /* Reverse mode of x(A, b) = C^{-1} A^T b.  With lambda = C^{-1} grad_x solved by the
  * same preconditioned CG to rtol:
@@ -207,9 +220,11 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
  * b, x, grad_x are the forward inputs/outputs (column-major, host or device);
  * grad_b or grad_vals may be NULL to skip them.  On a batched handle the adjoint solves of
  * all (problem, right-hand side) pairs run together on the block path (nrhs <= 32), each
- * to its own test relative to its ||grad_x||; grad_vals is summed over the pairs. */
+ * to its own test relative to its ||grad_x||; grad_vals is summed over the pairs.
+ * stream: the caller's stream, ordered against as in ls_solve. */
 ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x,
-                      int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info);
+                      int nrhs, double rtol, double* grad_b, double* grad_vals, ls_info* info,
+                      void* stream);
 
 /* Replace the values of A (same pattern; val[nnz] in the caller's CSR order, host or
  * device) in the operator the solves apply; the preconditioner built by ls_setup is

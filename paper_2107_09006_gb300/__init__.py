@@ -23,7 +23,7 @@ _PREC = {"f64": LS_PREC_F64, "f32": LS_PREC_F32, "bf16": LS_PREC_BF16}
 
 
 class ls_options(ctypes.Structure):
-    _fields_ = [("tau", ctypes.c_double), ("nev_max", ctypes.c_int), ("delta_rel", ctypes.c_double),
+    _fields_ = [("nev_max", ctypes.c_int), ("delta_rel", ctypes.c_double),
                 ("s_rel", ctypes.c_double), ("factor_prec", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
@@ -58,12 +58,12 @@ def _load():
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     sig = {
         "ls_default_options": (None, [ctypes.POINTER(ls_options)]),
-        "ls_setup": (ctypes.c_int, [i64, i64, vp, vp, vp, i32, vp, ctypes.c_int, ctypes.POINTER(ls_options), vp,
+        "ls_setup": (ctypes.c_int, [i64, i64, vp, vp, vp, i32, vp, ctypes.c_int, dbl, ctypes.POINTER(ls_options), vp,
                                     ctypes.POINTER(vp)]),
-        "ls_setup_batched": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, i32, vp, ctypes.c_int,
+        "ls_setup_batched": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, i32, vp, ctypes.c_int, dbl,
                                             ctypes.POINTER(ls_options), vp, ctypes.POINTER(vp)]),
-        "ls_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, dbl, vp, ctypes.POINTER(ls_info)]),
-        "ls_backward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, dbl, vp, vp, ctypes.POINTER(ls_info)]),
+        "ls_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, dbl, vp, ctypes.POINTER(ls_info), vp]),
+        "ls_backward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, dbl, vp, vp, ctypes.POINTER(ls_info), vp]),
         "ls_free": (None, [vp]),
         "ls_last_error": (ctypes.c_char_p, []),
         "ls_handle_info": (ctypes.c_int, [vp, ctypes.POINTER(ls_info)]),
@@ -121,16 +121,17 @@ def ls_default_options(**kw) -> ls_options:
     return o
 
 
-def ls_setup(m, n, row_ptr, col, val, nparts, part, overlap=1, opt=None, stream=None):
-    """Build the two-level preconditioner; returns the opaque handle (an int)."""
+def ls_setup(m, n, row_ptr, col, val, nparts, part, overlap=1, tau=0.0, opt=None, stream=None):
+    """Build the two-level preconditioner (threshold tau; tau <= 0: automatic); returns
+    the opaque handle (an int)."""
     h = ctypes.c_void_p()
     o = opt if opt is not None else ls_default_options()
     _check(_lib.ls_setup(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), int(nparts), _ptr(part),
-                         int(overlap), ctypes.byref(o), stream, ctypes.byref(h)))
+                         int(overlap), float(tau), ctypes.byref(o), stream, ctypes.byref(h)))
     return h.value
 
 
-def ls_setup_batched(m_off, n_off, row_ptr, col, val, nparts, part, overlap=1, opt=None, stream=None):
+def ls_setup_batched(m_off, n_off, row_ptr, col, val, nparts, part, overlap=1, tau=0.0, opt=None, stream=None):
     """Batched setup of independent problems given as one block-diagonal CSR matrix;
     m_off, n_off: host int64 offsets of the problems' rows and columns."""
     mo = np.ascontiguousarray(m_off, dtype=np.int64)
@@ -138,13 +139,16 @@ def ls_setup_batched(m_off, n_off, row_ptr, col, val, nparts, part, overlap=1, o
     h = ctypes.c_void_p()
     o = opt if opt is not None else ls_default_options()
     _check(_lib.ls_setup_batched(int(len(mo) - 1), _ptr(mo), _ptr(no), _ptr(row_ptr), _ptr(col), _ptr(val),
-                                 int(nparts), _ptr(part), int(overlap), ctypes.byref(o), stream, ctypes.byref(h)))
+                                 int(nparts), _ptr(part), int(overlap), float(tau), ctypes.byref(o), stream,
+                                 ctypes.byref(h)))
     return h.value
 
 
-def ls_solve(h, b, nrhs, rtol, x, raise_on_fail=True) -> dict:
+def ls_solve(h, b, nrhs, rtol, x, raise_on_fail=True, stream=None) -> dict:
+    """``stream``: the caller's raw cudaStream_t to order the call against (None: the
+    legacy default stream)."""
     info = ls_info()
-    st = _lib.ls_solve(h, _ptr(b), int(nrhs), float(rtol), _ptr(x), ctypes.byref(info))
+    st = _lib.ls_solve(h, _ptr(b), int(nrhs), float(rtol), _ptr(x), ctypes.byref(info), stream)
     if raise_on_fail:
         _check(st)
     d = info.as_dict()
@@ -152,10 +156,10 @@ def ls_solve(h, b, nrhs, rtol, x, raise_on_fail=True) -> dict:
     return d
 
 
-def ls_backward(h, b, x, grad_x, nrhs, rtol, grad_b=None, grad_vals=None) -> dict:
+def ls_backward(h, b, x, grad_x, nrhs, rtol, grad_b=None, grad_vals=None, stream=None) -> dict:
     info = ls_info()
     _check(_lib.ls_backward(h, _ptr(b), _ptr(x), _ptr(grad_x), int(nrhs), float(rtol), _ptr(grad_b),
-                            _ptr(grad_vals), ctypes.byref(info)))
+                            _ptr(grad_vals), ctypes.byref(info), stream))
     return info.as_dict()
 
 

@@ -1034,8 +1034,8 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     double thr_max = 0.0;
     for (int q = 0; q < h->nprob; ++q) {
       double thr = 0.0;
-      if (h->opt.tau > 0) {
-        thr = 1.0 / h->opt.tau;
+      if (h->tau > 0) {
+        thr = 1.0 / h->tau;
       } else {
         for (int i = h->h_N_off[q]; i < h->h_N_off[q + 1]; ++i) {
           const int64_t ni = hs.om_off[i + 1] - hs.om_off[i];
@@ -1192,11 +1192,34 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
 
 }  // namespace
 
+namespace {
+
+// Orders one call's device work, which runs on the handle's stream, between the work
+// the caller queued on its own stream before the call and what it queues there after:
+// an event recorded on the caller's stream that the handle's stream waits for at entry,
+// and one recorded on the handle's stream that the caller's waits for at exit.
+struct CallerOrder {
+  ls_handle* h;
+  cudaStream_t caller;
+  bool joined = false;
+  CallerOrder(ls_handle* h_, void* s) : h(h_), caller(static_cast<cudaStream_t>(s)) {
+    if (caller == h->st) return;
+    if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->ev_join, caller));
+    CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    joined = true;
+  }
+  ~CallerOrder() {
+    if (joined && cudaEventRecord(h->ev_join, h->st) == cudaSuccess) cudaStreamWaitEvent(caller, h->ev_join, 0);
+  }
+};
+
+}  // namespace
+
 extern "C" {
 
 void ls_default_options(ls_options* o) {
   if (!o) return;
-  o->tau = 0.0;
   o->nev_max = 16;
   o->delta_rel = 1e-10;
   o->s_rel = 1e-8;
@@ -1222,7 +1245,8 @@ namespace {
 
 ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off, int64_t m, int64_t n,
                       const int64_t* row_ptr, const int32_t* col, const double* val, int32_t nparts,
-                      const int32_t* part, int overlap, const ls_options* opt, void* stream, ls_handle** out) {
+                      const int32_t* part, int overlap, double tau, const ls_options* opt, void* stream,
+                      ls_handle** out) {
   if (out) *out = nullptr;
   return guarded([&]() -> ls_status {
     if (!out || !row_ptr || !part || (!col && m > 0) || (!val && m > 0))
@@ -1247,7 +1271,9 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
       throw LsError(LS_ERR_INVALID, "spmv must be 0 or a sparse-product kernel code");
     if (h->opt.variant != 0 && nprob > 1)
       throw LsError(LS_ERR_UNSUPPORTED, "the balanced and deflated variants are implemented for single-problem handles");
-    if (h->opt.tau >= 1.0) throw LsError(LS_ERR_UNSUPPORTED, "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
+    if (!(tau < 1.0)) throw LsError(tau >= 1.0 ? LS_ERR_UNSUPPORTED : LS_ERR_INVALID,
+                                    "tau >= 1 keeps the eigenvalue-1 cluster, which the device Lanczos cannot resolve");
+    h->tau = tau;
     CK(cudaGetDevice(&h->dev));
     if (stream) {
       h->st = (cudaStream_t)stream;
@@ -1280,28 +1306,29 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
 }  // namespace
 
 ls_status ls_setup(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
-                   int32_t nparts, const int32_t* part, int overlap, const ls_options* opt, void* stream,
+                   int32_t nparts, const int32_t* part, int overlap, double tau, const ls_options* opt, void* stream,
                    ls_handle** out) {
-  return setup_entry(1, nullptr, nullptr, m, n, row_ptr, col, val, nparts, part, overlap, opt, stream, out);
+  return setup_entry(1, nullptr, nullptr, m, n, row_ptr, col, val, nparts, part, overlap, tau, opt, stream, out);
 }
 
 ls_status ls_setup_batched(int32_t nprob, const int64_t* m_off, const int64_t* n_off, const int64_t* row_ptr,
                            const int32_t* col, const double* val, int32_t nparts, const int32_t* part, int overlap,
-                           const ls_options* opt, void* stream, ls_handle** out) {
+                           double tau, const ls_options* opt, void* stream, ls_handle** out) {
   if (nprob < 1 || !m_off || !n_off) {
     if (out) *out = nullptr;
     g_err = "nprob must be positive and m_off, n_off non-null";
     return LS_ERR_INVALID;
   }
-  return setup_entry(nprob, m_off, n_off, m_off[nprob], n_off[nprob], row_ptr, col, val, nparts, part, overlap, opt,
-                     stream, out);
+  return setup_entry(nprob, m_off, n_off, m_off[nprob], n_off[nprob], row_ptr, col, val, nparts, part, overlap, tau,
+                     opt, stream, out);
 }
 
-ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x, ls_info* info) {
+ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double* x, ls_info* info, void* stream) {
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
     if (!(rtol > 0) && h->opt.fixed_iters <= 0) throw LsError(LS_ERR_INVALID, "rtol must be positive");
     CK(cudaSetDevice(h->dev));
+    CallerOrder order(h, stream);
     if (nrhs > 1 || h->nprob > 1) {
       if (h->opt.solver != 0)
         throw LsError(LS_ERR_UNSUPPORTED, "the LSQR and GMRES outer solvers take one right-hand side of a single "
@@ -1324,14 +1351,12 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
 }
 
 ls_status ls_backward(ls_handle* h, const double* b, const double* x, const double* grad_x, int nrhs, double rtol,
-                      double* grad_b, double* grad_vals, ls_info* info) {
+                      double* grad_b, double* grad_vals, ls_info* info, void* stream) {
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || !grad_x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
-    if (h->nprob > 1) {
-      CK(cudaSetDevice(h->dev));
-      return block_backward(h, b, x, grad_x, nrhs, rtol, grad_b, grad_vals, info);
-    }
     CK(cudaSetDevice(h->dev));
+    CallerOrder order(h, stream);
+    if (h->nprob > 1) return block_backward(h, b, x, grad_x, nrhs, rtol, grad_b, grad_vals, info);
     cudaStream_t st = h->st;
     ls_status last = LS_OK;
     DevBuf<double> xk, lam, mu, tmp, gperm, gout;

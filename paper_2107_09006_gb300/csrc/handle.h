@@ -127,7 +127,9 @@ struct ls_handle {
   int dev = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  cudaEvent_t ev_join = nullptr;  // orders a call against the caller's stream (ls_solve, ls_backward)
   ls_options opt{};
+  double tau = 0.0;  // threshold given to ls_setup (<= 0: automatic)
   int64_t m = 0, n = 0, nnz = 0;
   int N = 0, lanes_csr = 8, lanes_csc = 32, grid_csr = 0, grid_csc = 0, prec = 0;
 
@@ -202,6 +204,7 @@ struct ls_handle {
     if (gexec) cudaGraphExecDestroy(gexec);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (pin) cudaFreeHost(pin);
     if (own_stream && st) cudaStreamDestroy(st);
   }

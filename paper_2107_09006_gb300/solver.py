@@ -20,7 +20,8 @@ def _dev(a, dtype, device):
 class Solver:
     """Owns one ls_handle: ``Solver(m, n, row_ptr, col, val, part, nparts, **options)``.
 
-    Options are the fields of ls_options (tau, nev_max, delta_rel, s_rel, factor_prec
+    ``tau`` is ls_setup's threshold (keep lambda > 1/tau; <= 0: automatic).  The other
+    options are the fields of ls_options (nev_max, delta_rel, s_rel, factor_prec
     ('f64' | 'f32' | 'bf16'), maxit, coarse, fixed_iters, eig_maxit, eig_tol,
     use_graph, time_kernels, equilibrate, variant (0 additive, 1 balanced second level,
     2 RAS with the deflated second level), solver (0 PCG, 1 preconditioned LSQR, 2
@@ -32,7 +33,7 @@ class Solver:
     """
 
     def __init__(self, m, n, row_ptr, col, val, part, nparts, device="cuda", stream=None, problems=None,
-                 **options):
+                 tau=0.0, **options):
         """``stream``: a torch.cuda.Stream the handle runs on (None: its own stream).
         ``problems``: None, or (m_off, n_off) row/column offsets of independent problems
         stored block-diagonally in (row_ptr, col, val) (ls_setup_batched)."""
@@ -44,16 +45,17 @@ class Solver:
         self.part = _dev(part, torch.int32, self.device)
         self.nparts = int(nparts)
         self.opt = ls_default_options(**options)
+        self.tau = float(tau)
         self.nprob = 1 if problems is None else len(problems[0]) - 1
         with torch.cuda.device(self.device):
             torch.cuda.synchronize(self.device)  # the inputs above were written on torch's stream
             s = stream.cuda_stream if stream is not None else None
             if problems is None:
                 self.h = ls_setup(self.m, self.n, self.row_ptr, self.col, self.val, self.nparts, self.part, 1,
-                                  self.opt, s)
+                                  self.tau, self.opt, s)
             else:
                 self.h = ls_setup_batched(problems[0], problems[1], self.row_ptr, self.col, self.val, self.nparts,
-                                          self.part, 1, self.opt, s)
+                                          self.part, 1, self.tau, self.opt, s)
         self.stream = stream
 
     def close(self):
@@ -75,13 +77,17 @@ class Solver:
         if self.stream is None:
             torch.cuda.current_stream(self.device).synchronize()
 
+    def _torch_stream(self):
+        """torch's current stream on the solver's device, which the solve and the
+        adjoint order themselves against (the inputs were written there)."""
+        return torch.cuda.current_stream(self.device).cuda_stream
+
     def solve(self, b, rtol=1e-8, raise_on_fail=True):
         """x = argmin ||A x - b|| for b of shape [m] or [nrhs, m] (one right-hand side per row)."""
         b = _dev(b, torch.float64, self.device)
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         x = torch.empty((self.n,) if b.dim() == 1 else (nrhs, self.n), dtype=torch.float64, device=self.device)
-        self._fence()
-        info = ls_solve(self.h, b, nrhs, rtol, x, raise_on_fail)
+        info = ls_solve(self.h, b, nrhs, rtol, x, raise_on_fail, stream=self._torch_stream())
         return x, info
 
     def backward(self, b, x, grad_x, rtol=1e-10, want_b=True, want_vals=True):
@@ -91,8 +97,7 @@ class Solver:
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         gb = torch.empty_like(b) if want_b else None
         gv = torch.empty(self.val.shape[0], dtype=torch.float64, device=self.device) if want_vals else None
-        self._fence()
-        info = ls_backward(self.h, b, x, g, nrhs, rtol, gb, gv)
+        info = ls_backward(self.h, b, x, g, nrhs, rtol, gb, gv, stream=self._torch_stream())
         return gb, gv, info
 
     def update_values(self, val):

@@ -177,25 +177,21 @@ def _coeffs(case, M):
 
 @pytest.mark.parametrize("prec,tol", [("f32", 1e-8), ("bf16", 1e-8)])
 def test_mixed_forms_meet_tolerance(prec, tol):
+    """The mixed forms reach the true-residual test, and their error against the FP64
+    solution (oracle PCG to 1e-13) is at most 10x the error of the oracle's own FP64 PCG
+    stopped at the same tolerance: the low-precision local factors cost no accuracy
+    beyond what the stopping test allows."""
     c = _mid()
     S = c.solver(factor_prec=prec)
     x, info = S.solve(c.b, rtol=tol)
     assert info["relres_true"] <= tol
     M = c.oracle()
     xo, _ = O.pcg(c.A, c.b, M.apply, rtol=1e-13)
-    # error against the FP64 solution is bounded by kappa(C) times the residual tolerance
-    kappa = _kappa_C(c.A)
-    assert rel(x.cpu().numpy(), xo) <= kappa * tol
+    xt, _ = O.pcg(c.A, c.b, M.apply, rtol=tol)
+    e_mixed, e_fp64 = rel(x.cpu().numpy(), xo), rel(xt, xo)
+    print(f"{prec}: error {e_mixed:.2e} against the FP64 oracle's {e_fp64:.2e} at rtol {tol:g}")
+    assert e_mixed <= 10 * e_fp64
     S.close()
-
-
-def _kappa_C(A):
-    """kappa(A^T A) from its extreme eigenvalues (ARPACK; shift-invert for the smallest)."""
-    import scipy.sparse.linalg as sla
-    C = (A.T @ A).tocsc()
-    lmax = sla.eigsh(C, k=1, which="LA", return_eigenvectors=False)[0]
-    lmin = sla.eigsh(C, k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
-    return float(lmax / lmin)
 
 
 def test_one_subdomain_exact():
@@ -244,4 +240,63 @@ def test_errors_are_reported():
     S = c.solver(maxit=2)
     x, info = S.solve(c.b, rtol=1e-12, raise_on_fail=False)
     assert info["status"] == L.LS_ERR_NOT_CONVERGED and info["iters"] == 2
+    S.close()
+
+
+def test_tau_argument_selects_like_oracle():
+    """ls_setup's threshold argument (Algorithm 1's input tau): with 1/tau placed in a gap
+    of the local spectra, every subdomain keeps exactly the oracle's vectors."""
+    c = _mid()
+    M0 = c.oracle()
+    lam = np.sort(np.concatenate([np.asarray(l[: c.nev + 1]) for l in M0.lams]))[::-1]
+    lam = lam[(lam > 1.05) & (lam < lam[0])]
+    gaps = lam[:-1] / lam[1:]
+    j = int(np.argmax(gaps[: max(1, len(gaps) // 2)]))  # a wide gap among the larger eigenvalues
+    thr = float(np.sqrt(lam[j] * lam[j + 1]))
+    tau = 1.0 / thr
+    M = O.build_two_level(c.A, c.part, c.N, tau=tau, nev_max=c.nev)
+    S = c.solver(tau=tau)
+    assert S.sizes()[:, 3].tolist() == list(M.ks)
+    assert S.info()["n0"] == M.n0 and 0 < M.n0
+    assert abs(S.info()["tau_used"] - tau) <= 1e-15 * tau
+    r = np.random.default_rng(8).standard_normal(c.n)
+    assert rel(S.apply_preconditioner(r, 0).cpu().numpy(), M.apply(r)) < 1e-9
+    S.close()
+    for bad, status in ((1.0, L.LS_ERR_UNSUPPORTED), (float("nan"), L.LS_ERR_INVALID)):
+        with pytest.raises(L.LSError) as e:
+            c.solver(tau=bad)
+        assert e.value.status == status
+
+
+def test_solve_orders_against_caller_stream():
+    """ls_solve(..., stream): the solve starts after the work queued on the caller's
+    stream (here b is written there behind a ~20 ms device sleep, without any host
+    synchronisation) and the caller's later work sees x; the same for ls_backward."""
+    c = _tiny()
+    S = c.solver()
+    xo, _ = S.solve(c.b, rtol=1e-10)
+    side = torch.cuda.Stream()
+    b_src = torch.as_tensor(c.b, device="cuda")
+    torch.cuda.synchronize()
+    b = torch.zeros(c.m, dtype=torch.float64, device="cuda")
+    x = torch.zeros(c.n, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(40_000_000)
+        b.copy_(b_src)
+        L.ls_solve(S.h, b, 1, 1e-10, x, stream=side.cuda_stream)
+        x2 = x.clone()  # queued on the caller's stream after the call
+    side.synchronize()
+    assert rel(x2.cpu().numpy(), xo.cpu().numpy()) < 1e-12
+    g = torch.zeros(c.n, dtype=torch.float64, device="cuda")
+    g_src = torch.as_tensor(np.random.default_rng(9).standard_normal(c.n), device="cuda")
+    gb_ref, _, _ = S.backward(c.b, xo, g_src, rtol=1e-10)
+    gb = torch.zeros(c.m, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(40_000_000)
+        g.copy_(g_src)
+        L.ls_backward(S.h, b, x, g, 1, 1e-10, gb, None, stream=side.cuda_stream)
+        gb2 = gb.clone()
+    side.synchronize()
+    assert rel(gb2.cpu().numpy(), gb_ref.cpu().numpy()) < 1e-12
     S.close()
