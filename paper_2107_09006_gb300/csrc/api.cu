@@ -92,6 +92,13 @@ lsq::DotSite site(ls_handle* h, int slot, int counter, int out2 = 0) {
 
 bool balanced(const ls_handle* h) { return h->opt.variant == 1 && h->coarse && h->n0 > 0; }
 
+// Timing mark k of an iteration: an event record, or a global-timer stamp while the
+// device-side loop's body is being captured.
+void mark(ls_handle* h, int k) {
+  if (h->stamping) lsq::launch_stamp(h->stamps.p, h->ctr.p, h->hist_cap, k, k == 5 ? 1 : 0, h->st);
+  else record_event(h->ev[k], h->st);
+}
+
 // y = local solves of rin (and, with_coarse, the fused coarse restriction r0 = R_0 rin)
 void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
   lsq::LocalArgs a{};
@@ -139,9 +146,9 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
   coarse_term(h, rin, h->bal_y.p);                                     // Q r
   apply_C(h, h->bal_y.p, h->bal_t.p);                                  // C Q r
   lsq::launch_axpby(h->n, 1.0, rin, -1.0, h->bal_t.p, h->bal_t.p, st);  // t = (I - CQ) r
-  if (timed) record_event(h->ev[2], st);
+  if (timed) mark(h, 2);
   launch_local(h, h->bal_t.p, false);
-  if (timed) record_event(h->ev[3], st);
+  if (timed) mark(h, 3);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
   s.z = h->bal_u.p;
@@ -149,7 +156,7 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
   lsq::launch_scatter(s, st);                                          // u = M_1 t
   apply_C(h, h->bal_u.p, h->bal_t.p);                                  // C u
   coarse_term(h, h->bal_t.p, h->bal_v.p);                              // Q C u
-  if (timed) record_event(h->ev[4], st);
+  if (timed) mark(h, 4);
   lsq::launch_combine3(h->n, h->bal_y.p, h->bal_u.p, h->bal_v.p, zout, rin, flex ? h->r_old.p : nullptr,
                        dots ? site(h, lsq::S_RZ, 2, lsq::S_RZO - lsq::S_RZ) : lsq::DotSite{}, st);
 }
@@ -166,11 +173,11 @@ void precond_deflated(ls_handle* h, const double* rin, double* zout, bool timed)
     lsq::launch_axpby(h->n, 1.0, rin, -1.0, h->bal_t.p, h->bal_t.p, st);  // (I - CQ) r
     t = h->bal_t.p;
   }
-  if (timed) record_event(h->ev[2], st);
+  if (timed) mark(h, 2);
   launch_local(h, t, false);
-  if (timed) record_event(h->ev[3], st);
+  if (timed) mark(h, 3);
   lsq::launch_ras_combine(h->n, h->own.p, h->ybuf.p, coarse ? h->bal_y.p : nullptr, zout, st);
-  if (timed) record_event(h->ev[4], st);
+  if (timed) mark(h, 4);
 }
 
 int deflated_launches(const ls_handle* h) { return 2 + ((h->coarse && h->n0 > 0) ? 6 : 0); }
@@ -188,12 +195,12 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
     return;
   }
   if (which != 0 && which != 1) throw LsError(LS_ERR_INVALID, "precond: which must be 0 or 1");
-  if (timed) record_event(h->ev[2], st);
+  if (timed) mark(h, 2);
   const bool use_coarse = h->coarse && h->n0 > 0 && which != 1;
   if (which != 2) launch_local(h, rin, use_coarse);
-  if (timed) record_event(h->ev[3], st);
+  if (timed) mark(h, 3);
   if (use_coarse) lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
-  if (timed) record_event(h->ev[4], st);
+  if (timed) mark(h, 4);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
   s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
@@ -211,19 +218,75 @@ int iteration_launches(const ls_handle* h) {
   return 6 + ((h->coarse && h->n0 > 0) ? 1 : 0);
 }
 
-void iteration(ls_handle* h, bool flex) {
+void iteration(ls_handle* h, bool flex, bool copy_scalars = true) {
   cudaStream_t st = h->st;
   const bool timed = h->opt.time_kernels != 0;
-  if (timed) record_event(h->ev[0], st);
+  if (timed) mark(h, 0);
   lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, h->grid_csr, st);
   lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, site(h, lsq::S_PW, 0), h->lanes_csc, h->grid_csc, st);
-  if (timed) record_event(h->ev[1], st);
+  if (timed) mark(h, 1);
   lsq::launch_cg_update(h->n, h->scal.p, h->p.p, h->w.p, h->x.p, h->r.p, flex ? h->r_old.p : nullptr,
                         site(h, lsq::S_RR, 1), h->ctr.p, h->ahist.p, h->hist_cap, st);
   precond(h, h->r.p, h->z.p, 0, true, flex, timed);
   lsq::launch_p_update(h->n, h->scal.p, h->ctr.p, h->bhist.p, h->hist_cap, h->z.p, h->p.p, 0, flex ? 1 : 0, st);
-  if (timed) record_event(h->ev[5], st);
-  CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
+  if (timed) mark(h, 5);
+  if (copy_scalars) CK(cudaMemcpyAsync(h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT, cudaMemcpyDeviceToHost, st));
+}
+
+// Builds h->gloop: while (loop test) { one PCG iteration }, then the scalar slots to the
+// host.  The body is captured from the same launch sequence as iteration(); the loop test
+// kernel sets the while condition from the device scalars, so the host waits once per
+// pass of the loop instead of once per iteration.  Returns false (and leaves gloop null)
+// when the graph cannot be built, e.g. on a driver without conditional nodes.
+bool build_loop_graph(ls_handle* h, bool flex, int limit) {
+  cudaStream_t st = h->st;
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  bool ok = false;
+  do {
+    cudaGraphConditionalHandle hnd;
+    if (cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    h->stamping = h->opt.time_kernels != 0;
+    iteration(h, flex, false);
+    lsq::launch_cg_continue(h->scal.p, h->ctr.p, limit, hnd, st);
+    h->stamping = false;
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(st, &captured) != cudaSuccess) break;
+    size_t nnodes = 0;
+    if (cudaGraphGetNodes(body, nullptr, &nnodes) != cudaSuccess) break;
+    cudaGraphNode_t cnode;
+    if (cudaGraphAddMemcpyNode1D(&cnode, g, &wnode, 1, h->pin, h->scal.p, sizeof(double) * lsq::S_NSLOT,
+                                 cudaMemcpyDeviceToHost) != cudaSuccess)
+      break;
+    if (cudaGraphInstantiate(&h->gloop, g, 0) != cudaSuccess) {
+      h->gloop = nullptr;
+      break;
+    }
+    h->loop_kernels = (int)nnodes;
+    ok = true;
+  } while (false);
+  h->stamping = false;
+  cudaGraphDestroy(g);
+  if (!ok) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(st, &junk);
+      if (junk) cudaGraphDestroy(junk);
+    }
+    cudaGetLastError();
+  }
+  return ok;
 }
 
 // Reads one scalar slot of the device CG state (synchronising the stream).
@@ -237,6 +300,7 @@ double dev_sum(ls_handle* h, int slot = lsq::S_TMP) {
 // ||g - C x||^2 into the host: mode 0 as ||A^T (b - A x)||^2, mode 1 as ||g - A^T (A x)||^2.
 // Leaves the residual vector in h->w; adds the kernels it launched to *launches.
 double true_residual(ls_handle* h, int mode, int* launches) {
+  Phase phase("true residual");
   cudaStream_t st = h->st;
   lsq::launch_spmv_csr(csr(h), h->x.p, h->q.p, h->lanes_csr, h->grid_csr, st);
   if (mode == 0) {
@@ -299,43 +363,85 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   int it = 0, restarts = 0;
   double rr = gg;
   bool graph_this = h->opt.use_graph != 0;
+  bool loop_this = graph_this;
+  // the device-side loop's test: (rtol ||g||)^2 on the recursive residual (none with
+  // fixed_iters); the host applies the same test to the same double
+  const double thr2 = (rtol * gn) * (rtol * gn);
+  lsq::launch_fill(1, fixed > 0 ? 0.0 : thr2, h->scal.p + lsq::S_THR, st);
+  launches += 1;
   while (it < maxit) {
-    if (graph_this) {
-      if (!h->gexec) {  // built once per handle: the iteration only touches fixed buffers
-        cudaGraph_t g;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        iteration(h, flex);
-        CK(cudaStreamEndCapture(st, &g));
-        cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          h->gexec = nullptr;
-          cudaGetLastError();
-          graph_this = false;
+    int done_now = 1;  // iterations this pass ran
+    if (loop_this) {
+      if (!h->gloop) {  // built once per handle: the loop only touches fixed buffers
+        if (timed && !h->stamps.p) h->stamps.alloc((size_t)h->hist_cap * 8);
+        if (!build_loop_graph(h, flex, maxit)) {
+          loop_this = false;
           continue;
         }
       }
-      CK(cudaGraphLaunch(h->gexec, st));
+      {
+        Phase phase("PCG loop pass (device-side while graph)");
+        CK(cudaGraphLaunch(h->gloop, st));
+        CK(cudaStreamSynchronize(st));
+      }
+      check_launch("CG loop");
+      done_now = (int)h->pin[lsq::S_ITS] - it;
+      if (done_now < 1) throw LsError(LS_ERR_CUDA, "the device-side CG loop ran no iteration");
+      launches += done_now * h->loop_kernels;
+      if (timed) {
+        std::vector<unsigned long long> tsm((size_t)done_now * 8);
+        const int first = std::min(it, h->hist_cap);
+        const int cnt = std::max(0, std::min(it + done_now, h->hist_cap) - first);
+        if (cnt > 0) {
+          CK(cudaMemcpy(tsm.data(), h->stamps.p + (size_t)first * 8, sizeof(unsigned long long) * 8 * cnt,
+                        cudaMemcpyDeviceToHost));
+          for (int j = 0; j < cnt; ++j) {
+            const unsigned long long* t = tsm.data() + (size_t)j * 8;
+            inf.ms_spmv += (t[1] - t[0]) * 1e-6;
+            inf.ms_local += (t[3] - t[2]) * 1e-6;
+            inf.ms_coarse += (t[4] - t[3]) * 1e-6;
+            inf.ms_iter += (t[5] - t[0]) * 1e-6;
+          }
+        }
+      }
     } else {
-      iteration(h, flex);
+      if (graph_this) {
+        if (!h->gexec) {  // built once per handle: the iteration only touches fixed buffers
+          cudaGraph_t g;
+          CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          iteration(h, flex);
+          CK(cudaStreamEndCapture(st, &g));
+          cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+          cudaGraphDestroy(g);
+          if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            cudaGetLastError();
+            graph_this = false;
+            continue;
+          }
+        }
+        CK(cudaGraphLaunch(h->gexec, st));
+      } else {
+        iteration(h, flex);
+      }
+      CK(cudaStreamSynchronize(st));
+      check_launch("CG iteration");
+      launches += iteration_launches(h);
+      if (timed) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+        CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
+        CK(cudaEventElapsedTime(&c, h->ev[3], h->ev[4]));
+        inf.ms_spmv += a;
+        inf.ms_local += b;
+        inf.ms_coarse += c;
+        float d = 0.f;
+        CK(cudaEventElapsedTime(&d, h->ev[0], h->ev[5]));
+        inf.ms_iter += d;
+      }
     }
-    CK(cudaStreamSynchronize(st));
-    check_launch("CG iteration");
-    ++it;
-    launches += iteration_launches(h);
-    inf.local_launches += 1;
-    if (timed) {
-      float a = 0.f, b = 0.f, c = 0.f;
-      CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-      CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
-      CK(cudaEventElapsedTime(&c, h->ev[3], h->ev[4]));
-      inf.ms_spmv += a;
-      inf.ms_local += b;
-      inf.ms_coarse += c;
-      float d = 0.f;
-      CK(cudaEventElapsedTime(&d, h->ev[0], h->ev[5]));
-      inf.ms_iter += d;
-    }
+    it += done_now;
+    inf.local_launches += done_now;
     rr = h->pin[lsq::S_RR];
     if (h->pin[lsq::S_ERR] != 0.0)
       throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up at iteration " +
@@ -343,7 +449,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     if (h->pin[lsq::S_FLAG] != 0.0 || !std::isfinite(rr))
       throw LsError(LS_ERR_NONFINITE, "CG breakdown: non-finite or non-positive p.Cp at iteration " + std::to_string(it));
     if (fixed > 0) continue;
-    if (std::sqrt(rr) <= rtol * gn) {
+    if (rr <= thr2) {
       const double tt = true_residual(h, mode, &launches);
       inf.relres_true = std::sqrt(tt) / gn;
       if (std::sqrt(tt) <= rtol * gn) { converged = true; break; }
@@ -451,7 +557,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
   double rel = 1.0;
   int it = 0;
   while (it < maxit) {
-    if (timed) record_event(h->ev[0], st);
+    if (timed) mark(h, 0);
     // beta u = A v - alpha u
     lsq::launch_spmv_csr(csr(h), h->lq_v.p, h->q.p, h->lanes_csr, h->grid_csr, st);
     if (timed) record_event(h->ev[6], st);
@@ -466,7 +572,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     // alpha v = M^{-1} (A^T u - beta q)
     if (timed) record_event(h->ev[7], st);
     lsq::launch_spmv_csc(csc(h), h->lq_u.p, h->lq_s.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, st);
-    if (timed) record_event(h->ev[1], st);
+    if (timed) mark(h, 1);
     lsq::launch_axpby(n, 1.0, h->lq_s.p, -beta, h->lq_q.p, h->lq_s.p, st);
     precond(h, h->lq_s.p, h->lq_t.p, 0, true, false, timed);
     alpha = std::sqrt(dev_sum(h, lsq::S_RZ));
@@ -484,7 +590,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     phibar = sn * phibar;
     lsq::launch_lsqr_step(n, 1.0 / alpha, phi / rho, theta / rho, h->lq_t.p, h->lq_s.p, h->lq_v.p, h->lq_q.p,
                           h->x.p, h->lq_w.p, st);
-    if (timed) record_event(h->ev[5], st);
+    if (timed) mark(h, 5);
     ++it;
     launches += 6 + pl + 1;
     inf.local_launches += 1;
@@ -585,11 +691,11 @@ ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
       double* vj = V + (int64_t)j * n;
       double* zj = Z + (int64_t)j * n;
       double* w = V + (int64_t)(j + 1) * n;
-      if (timed) record_event(h->ev[0], st);
+      if (timed) mark(h, 0);
       precond(h, vj, zj, 0, false, false, timed);
       if (timed) record_event(h->ev[6], st);
       apply_C(h, zj, w);
-      if (timed) record_event(h->ev[1], st);
+      if (timed) mark(h, 1);
       lsq::launch_multi_dot(n, V, n, j + 1, w, h->gm_part.p, h1, st);
       lsq::launch_multi_axpy(n, V, n, j + 1, h1, -1.0, w, st);
       lsq::launch_multi_dot(n, V, n, j + 1, w, h->gm_part.p, h2, st);
@@ -743,6 +849,7 @@ void autotune_spmv(ls_handle* h) {
 void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, const double* val_in,
               const int32_t* part_in) {
   const double t_begin = now_s();
+  Phase phase("ls_setup: inputs and index sets (host)");
   cudaStream_t st = h->st;
   std::vector<int64_t> hrp = to_host(row_ptr_in, (size_t)h->m + 1);
   const int64_t nnz = hrp[h->m];
@@ -808,6 +915,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->lanes_csc = pow2_lanes((double)nnz / (double)h->n);
 
   // matrix copies
+  phase.next("ls_setup: matrix copies and sparse-product autotuning");
   h->row_ptr.upload(hrp, st);
   h->col.upload(hcol, st);
   h->val.upload(hval, st);
@@ -839,6 +947,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   autotune_spmv(h);
 
   // local plan
+  phase.next("ls_setup: local matrices and Cholesky factors");
   h->total_local = hs.om_off[N];
   h->total_blocks = hs.blk_off[N];
   h->fac_elems = hs.fac_elems;
@@ -985,6 +1094,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->n0 = 0;
   if (h->coarse) {
     const double te0 = now_s();
+    phase.next("ls_setup: local eigensolves and coarse operator");
     Bidiag.alloc((size_t)h->total_blocks * 32);
     lsq::launch_band_cholesky(plan, Bst.p, Bidiag.p, dinv.p, status.p, st);
     CK(cudaMemcpyAsync(hst.data(), status.p, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
@@ -1328,6 +1438,7 @@ ls_status ls_solve(ls_handle* h, const double* b, int nrhs, double rtol, double*
     if (!h || !b || !x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
     if (!(rtol > 0) && h->opt.fixed_iters <= 0) throw LsError(LS_ERR_INVALID, "rtol must be positive");
     CK(cudaSetDevice(h->dev));
+    Phase phase("ls_solve");
     CallerOrder order(h, stream);
     if (nrhs > 1 || h->nprob > 1) {
       if (h->opt.solver != 0)
@@ -1355,6 +1466,7 @@ ls_status ls_backward(ls_handle* h, const double* b, const double* x, const doub
   return guarded([&]() -> ls_status {
     if (!h || !b || !x || !grad_x || nrhs < 1) throw LsError(LS_ERR_INVALID, "null handle/pointer or nrhs < 1");
     CK(cudaSetDevice(h->dev));
+    Phase phase("ls_backward");
     CallerOrder order(h, stream);
     if (h->nprob > 1) return block_backward(h, b, x, grad_x, nrhs, rtol, grad_b, grad_vals, info);
     cudaStream_t st = h->st;

@@ -3,6 +3,7 @@
 // multi right-hand-side solve in block.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <stdexcept>
@@ -60,6 +61,24 @@ struct DevBuf {
   void upload_from(const U* src, size_t count, cudaStream_t st) {
     alloc(count);
     if (count) CK(cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyDefault, st));
+  }
+};
+
+// NVTX ranges for the phases of setup and solve (seen by Nsight tools; a few
+// nanoseconds each when no tool is attached).  next() closes the current range and
+// opens the following one; the destructor closes the last, also on an error path.
+struct Phase {
+  bool open = false;
+  explicit Phase(const char* name) { next(name); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~Phase() {
+    if (open) nvtxRangePop();
   }
 };
 
@@ -175,6 +194,13 @@ struct ls_handle {
 
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // kernel timing
+  // The PCG loop as one graph: a conditional while node whose body is one iteration and
+  // the loop test, then the copy of the scalar slots to the host.  Timing inside it uses
+  // global-timer stamps (event records are not allowed in a conditional body).
+  cudaGraphExec_t gloop = nullptr;
+  int loop_kernels = 0;   // kernels of one loop-body pass
+  bool stamping = false;  // timing marks become stamp kernels (while the loop body is captured)
+  DevBuf<unsigned long long> stamps;  // [iteration][8] global-timer stamps of the loop
 
   // independent problems of one batched handle (block-diagonal A): problem q owns rows
   // [m_off[q], m_off[q+1]), columns [n_off[q], n_off[q+1]) and the subdomain ids
@@ -202,6 +228,7 @@ struct ls_handle {
   ~ls_handle() {
     if (dev >= 0) cudaSetDevice(dev);
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (gloop) cudaGraphExecDestroy(gloop);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     if (ev_join) cudaEventDestroy(ev_join);

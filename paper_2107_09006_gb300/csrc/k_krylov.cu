@@ -212,11 +212,26 @@ __global__ void __launch_bounds__(kThreads) k_p_update(int64_t n, double* scal, 
       const int it = *ctr;
       if (it >= 0 && it < cap) beta_hist[it] = beta;
       *ctr = it + 1;
+      scal[S_ITS] = (double)(it + 1);
       if (!isfinite(beta)) scal[S_FLAG] = 1.0;
     }
   }
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     p[k] = init ? z[k] : z[k] + beta * p[k];
+}
+
+__global__ void k_cg_continue(const double* scal, const int* ctr, int limit, cudaGraphConditionalHandle hnd) {
+  const double rr = scal[S_RR], thr = scal[S_THR];
+  bool go = scal[S_FLAG] == 0.0 && scal[S_ERR] == 0.0 && isfinite(rr) && *ctr < limit;
+  if (thr > 0.0 && rr <= thr) go = false;
+  cudaGraphSetConditional(hnd, go ? 1u : 0u);
+}
+
+__global__ void k_stamp(unsigned long long* stamps, const int* ctr, int cap, int k, int after) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  const int slot = *ctr - after;
+  if (slot >= 0 && slot < cap) stamps[(int64_t)slot * 8 + k] = t;
 }
 
 __global__ void __launch_bounds__(kThreads) k_dot(int64_t n, const double* __restrict__ a,
@@ -484,6 +499,15 @@ void launch_p_update(int64_t n, double* scal, int* ctr, double* beta_hist, int h
                      int init, int flex, cudaStream_t st) {
   k_p_update<<<grid_for(n, kThreads, kVecGrid), kThreads, 0, st>>>(n, scal, ctr, beta_hist, hist_cap, z, p, init,
                                                                    flex);
+}
+
+void launch_cg_continue(const double* scal, const int* ctr, int limit, cudaGraphConditionalHandle hnd,
+                        cudaStream_t st) {
+  k_cg_continue<<<1, 1, 0, st>>>(scal, ctr, limit, hnd);
+}
+
+void launch_stamp(unsigned long long* stamps, const int* ctr, int cap, int k, int after, cudaStream_t st) {
+  k_stamp<<<1, 1, 0, st>>>(stamps, ctr, cap, k, after);
 }
 
 void launch_dot(int64_t n, const double* a, const double* b, const DotSite& ds, cudaStream_t st) {

@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
 
   cons.start(tf, nb, CC);
   TA acc = 0;
+  TA acc4[4] = {0, 0, 0, 0};                        // FP64: four independent FMA chains
   TA xr[kT];                                        // rotated copy of x_b (vectorised path)
   // this thread's skew of 16-byte groups: consecutive threads read consecutive columns
   // (32 x ES bytes each), so eight threads of a quarter-warp hit eight distinct 16-byte
@@ -208,7 +209,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     const int phi = min(hi, offw);  // panel columns of this chunk: [lo, phi)
     const float* sc = a.tsc ? a.tsc + poff[b] / 1024 : nullptr;
     if (cons.sweep == 0) {
-      if (cons.k == cons.nchunks(b) - 1) acc = 0;
+      if (cons.k == cons.nchunks(b) - 1) {
+        acc = 0;
+        acc4[0] = acc4[1] = acc4[2] = acc4[3] = 0;
+      }
       TA* vw = v + t0 * kT;
       if constexpr (kVec) {
         // warp w takes the contiguous columns [c0, c0 + CPW) of the chunk (one BF16 tile)
@@ -231,13 +235,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           acc += sc ? (s0 + s1) * (TA)sc[c0 >> 5] : (s0 + s1);
         }
       } else {
-        for (int c = lo + w; c < phi; c += kWarps) {
-          TA p = Val<TF>::f(ch[(c - lo) * kT + lane]);
-          if (sc) p *= (TA)sc[c >> 5];
-          acc += p * vw[c];
+        // FP64: warp w takes the contiguous columns [c0, c0 + CPW) of the chunk, the
+        // window entries read two at a time, four independent FMA chains (the FP64 units
+        // are few, so a single dependent chain per thread leaves them idle)
+        const int c0 = lo + w * CPW;
+        const TF* colp = ch + (c0 - lo) * kT + lane;
+        if (c0 + CPW <= phi) {
+#pragma unroll
+          for (int j = 0; j < CPW; j += 2) {
+            const double2 v2 = *reinterpret_cast<const double2*>(vw + c0 + j);
+            acc4[(j >> 1) & 3] += Val<TF>::f(colp[j * kT]) * v2.x;
+            acc4[((j >> 1) + 2) & 3] += Val<TF>::f(colp[(j + 1) * kT]) * v2.y;
+          }
+        } else if (c0 < phi) {
+#pragma unroll
+          for (int j = 0; j < CPW; ++j)
+            if (c0 + j < phi) acc4[j & 3] += Val<TF>::f(colp[j * kT]) * vw[c0 + j];
         }
       }
       if (cons.k == 0) {
+        if constexpr (!kVec) acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
         red[w * 32 + lane] = acc;
         __syncthreads();
         const TF* D = ch + (offw - lo) * kT;  // inverse tile, column-major
@@ -359,11 +376,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
       TA s = 0;
       if (c < phi) {
         const TF* col = ch + cl * kT + g * RG;
-#pragma unroll 8
-        for (int u = 0; u < RG; ++u) {
-          const int r = (u + c) & (RG - 1);
-          s += Val<TF>::f(col[r]) * xv[g * RG + r];
+        TA s1 = 0;  // two FMA chains
+#pragma unroll
+        for (int u = 0; u < RG; u += 2) {
+          const int r0 = (u + c) & (RG - 1), r1 = (u + 1 + c) & (RG - 1);
+          s += Val<TF>::f(col[r0]) * xv[g * RG + r0];
+          s1 += Val<TF>::f(col[r1]) * xv[g * RG + r1];
         }
+        s += s1;
         if (sc) s *= (TA)sc[c >> 5];
       }
       if (G == 1) {

@@ -25,10 +25,12 @@ struct CscDev {
 // warp; -2 sliced ELL.
 inline bool valid_spmv_code(int c) { return (c >= -3 && c <= -1) || c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
-// Scalar slots of the CG state kept on the device (copied to the host each iteration).
+// Scalar slots of the CG state kept on the device (copied to the host when the host
+// needs them).  S_THR: squared residual threshold (rtol ||g||)^2 of the device loop (0: no
+// test); S_ITS: iterations completed, written by the beta update.
 enum {
   S_RZOLD = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_FLAG = 4, S_GG = 5, S_ERR = 6,
-  S_PW = 7, S_RZ = 8, S_RZO = 9, S_TMP = 10, S_NSLOT = 12
+  S_PW = 7, S_RZ = 8, S_RZO = 9, S_TMP = 10, S_THR = 11, S_ITS = 12, S_NSLOT = 14
 };
 constexpr int kMaxGrid = 65536;  // largest grid of a kernel that produces a dot product
 constexpr int kVecGrid = 1216;   // grid cap of the n-vector kernels (8 blocks of 256 per SM)
@@ -49,6 +51,15 @@ void launch_cg_update(int64_t n, double* scal, const double* p, const double* w,
 // beta from the scalar slots (plain or flexible form), p = z + beta p (init: p = z).
 void launch_p_update(int64_t n, double* scal, int* ctr, double* beta_hist, int hist_cap, const double* z, double* p,
                      int init, int flex, cudaStream_t st);
+// The loop test of the device-side PCG loop (a conditional while node of a CUDA graph):
+// continue while no breakdown or device timeout is flagged, the recursive residual
+// ||r||^2 = scal[S_RR] is above scal[S_THR] (when that is positive) and fewer than
+// `limit` iterations have run.
+void launch_cg_continue(const double* scal, const int* ctr, int limit, cudaGraphConditionalHandle hnd,
+                        cudaStream_t st);
+// Writes the global nanosecond timer into stamps[slot * 8 + k], slot = *ctr - after, when
+// 0 <= slot < cap (kernel timing inside graphs, where event records are not allowed).
+void launch_stamp(unsigned long long* stamps, const int* ctr, int cap, int k, int after, cudaStream_t st);
 void launch_dot(int64_t n, const double* a, const double* b, const DotSite& ds, cudaStream_t st);
 void launch_axpby(int64_t n, double alpha, const double* a, double beta, const double* b, double* out,
                   cudaStream_t st);

@@ -207,3 +207,44 @@ def test_batched_backward_matches_dense_gradient(batch):
             gsum += gvals
         assert rel(gv[e0:e1], gsum) < 1e-8, q
     S.close()
+
+
+def _round_tf32(a):
+    """Round to TF32 (10 explicit mantissa bits), to nearest with ties away from zero."""
+    u = a.astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def test_tf32_factor_error_stated(grid96):
+    """The block path applies FP32 local factors on TF32 tensor cores: the factor is
+    rounded to TF32 (unit roundoff 2^-11), the solution operand is split into a TF32 head
+    and tail (so it keeps ~21 bits) and the products accumulate in FP32.  This states that
+    error and checks it against a model computed from the oracle's own factors rounded to
+    TF32 and applied in FP64: the first PCG iterate x_1 = alpha_0 M^{-1} A^T b of the block
+    path (2 right-hand sides) lies within 10x the model's relative error of the FP64
+    oracle's, while the FP32 single-vector path (FP32 factors, no TF32 rounding) is at
+    least 20x closer than the model."""
+    import scipy.linalg as sl
+    d = grid96
+    A, M = d["A"], d["M"]
+    B2 = d["b"][:2]
+    xo = [O.pcg(A, B2[k], M.apply, fixed_iters=1)[0] for k in range(2)]
+    # the model: every local factor rounded to TF32, applied in FP64 (dense mode factors)
+    def apply_tf32(r):
+        z = np.zeros_like(r)
+        for idx, (c, lower) in M.local:
+            y = sl.cho_solve((_round_tf32(np.tril(c)) if lower else _round_tf32(np.triu(c)), lower), r[idx])
+            np.add.at(z, idx, y)
+        return z + M.apply_coarse(r)
+    xm = [O.pcg(A, B2[k], apply_tf32, fixed_iters=1)[0] for k in range(2)]
+    e_model = max(rel(xm[k], xo[k]) for k in range(2))
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16, factor_prec="f32", fixed_iters=1)
+    X, _ = S.solve(B2, rtol=1e-8)
+    e_block = max(rel(X[k].cpu().numpy(), xo[k]) for k in range(2))
+    e_single = max(rel(S.solve(B2[k], rtol=1e-8)[0].cpu().numpy(), xo[k]) for k in range(2))
+    print(f"first iterate vs FP64 oracle: TF32 block path {e_block:.2e}, FP32 single-vector path {e_single:.2e}, "
+          f"TF32-rounded-factor model {e_model:.2e}")
+    assert e_block <= 10 * e_model
+    assert e_single * 20 <= e_model
+    S.close()

@@ -300,3 +300,34 @@ def test_solve_orders_against_caller_stream():
     side.synchronize()
     assert rel(gb2.cpu().numpy(), gb_ref.cpu().numpy()) < 1e-12
     S.close()
+
+
+def test_device_loop_matches_host_loop():
+    """The PCG loop run on the device (a conditional graph node, one host wait per pass)
+    gives the same iterates, bit for bit, as the host-driven loop (one wait per
+    iteration): the same kernels in the same order, with deterministic reductions.  The
+    sparse-product kernel is fixed (option spmv) so that the handles do not each pick
+    their own by timing.  With kernel timing on, every iteration's local solve and
+    products are timed."""
+    c = _mid()
+    res = {}
+    for name, kw in (("host", dict(use_graph=0)), ("device", {}), ("device-timed", dict(time_kernels=1))):
+        kw = dict(kw, spmv=2)
+        for prec in ("f64", "f32"):
+            S = c.solver(factor_prec=prec, **kw)
+            x, info = S.solve(c.b, rtol=1e-10)
+            S2 = c.solver(factor_prec=prec, fixed_iters=7, **kw)
+            x7, i7 = S2.solve(c.b, rtol=1e-8)
+            res[name, prec] = (x.cpu().numpy(), info, x7.cpu().numpy(), i7)
+            S.close()
+            S2.close()
+    for prec in ("f64", "f32"):
+        xh, ih, x7h, i7h = res["host", prec]
+        for name in ("device", "device-timed"):
+            xd, idv, x7d, i7d = res[name, prec]
+            assert np.array_equal(xd, xh) and idv["iters"] == ih["iters"], (name, prec)
+            assert np.array_equal(x7d, x7h) and i7d["iters"] == i7h["iters"] == 7, (name, prec)
+            assert idv["relres_true"] <= 1e-10
+        it = res["device-timed", prec][1]
+        assert it["ms_local"] > 0 and it["ms_spmv"] > 0 and it["ms_iter"] >= it["ms_local"] + it["ms_spmv"]
+        assert it["local_launches"] == it["iters"] + 1 + it["restarts"]
