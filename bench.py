@@ -69,6 +69,9 @@ def parse():
                          "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
     ap.add_argument("--spmv", type=int, default=0,
                     help="solve mode: force one sparse-product kernel code for A and A^T (0: autotuned)")
+    ap.add_argument("--block-kernel", type=int, default=0,
+                    help="batch mode: local-solve kernel of the FP32 block path (0 timed choice, 1 TF32 mma.sync, "
+                         "2 tcgen05)")
     ap.add_argument("--nprob", type=int, default=64)
     ap.add_argument("--nrhs", type=int, default=32)
     return ap.parse_args()
@@ -650,7 +653,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     t = time.time()
     S = Solver(B.m, B.n, B.row_ptr, B.col, B.val, B.part, B.nparts, device=dev, stream=stream,
-               problems=(B.m_off, B.n_off), nev_max=args.nev, factor_prec=args.prec, time_kernels=1, maxit=500)
+               problems=(B.m_off, B.n_off), nev_max=args.nev, factor_prec=args.prec, time_kernels=1, maxit=500,
+               block_kernel=args.block_kernel)
     torch.cuda.synchronize(dev)
     setup = time.time() - t
     si, st = S.info(), S.storage()
@@ -709,6 +713,7 @@ def run_batch(args):
         "spmm_pair_ms_per_iter": inf["ms_spmv"] / max(inf["iters"], 1),
         "coarse_ms_per_iter": inf["ms_coarse"] / max(inf["iters"], 1),
         "launches_per_step": inf["launches"], "clocks": clocks,
+        "local_kernel": {0: "CUDA cores", 1: "TF32 mma.sync", 2: "tcgen05 (TMEM accumulator)"}[inf["local_kernel"]],
     }
     print(json.dumps(out), flush=True)
     S.close()

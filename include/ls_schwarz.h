@@ -107,6 +107,13 @@ typedef struct {
                           (after about two seconds), the kernel sets the error slot and
                           returns with nothing in flight, and the solve returns
                           LS_ERR_DEVICE_TIMEOUT.  The CUDA context stays usable.      */
+    int block_kernel;  /* local solve of the multi right-hand-side path with FP32 factors:
+                          0 (the default) times both at the first block solve and keeps
+                          the faster; 1 TF32 mma.sync tiles, left-looking sweeps; 2
+                          tcgen05 MMAs (M = 128, accumulator in tensor memory),
+                          right-looking sweeps (LS_ERR_UNSUPPORTED if the widest factor
+                          block row does not fit its shared-memory window).  Both round
+                          the factor to TF32.  ls_info.local_kernel reports the choice. */
 } ls_options;
 
 typedef struct {
@@ -131,6 +138,9 @@ typedef struct {
     int launches;            /* kernels launched by the last solve (all of this library's)  */
     double ms_iter;          /* with time_kernels: total ms of whole CG iterations (kernels) */
     int lanes_csr, lanes_csc;/* kernel codes of the products with A / A^T (option spmv)    */
+    int local_kernel;        /* local-solve kernel of the last solve: 0 the single-vector or
+                                CUDA-core block kernel, 1 TF32 mma.sync block kernel, 2
+                                tcgen05 block kernel                                       */
 } ls_info;
 
 typedef struct ls_handle ls_handle;
@@ -138,7 +148,8 @@ typedef struct ls_handle ls_handle;
 /* Fill *opt with the defaults: nev_max = 16, delta_rel = 1e-10,
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
- * equilibrate = 0, variant = 0, solver = 0, restart = 100. */
+ * equilibrate = 0, variant = 0, solver = 0, restart = 100, spmv = 0, test_stall = 0,
+ * block_kernel = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1, whose inputs are A, the subdomain count N and

@@ -28,7 +28,8 @@ class ls_options(ctypes.Structure):
                 ("coarse", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("eig_maxit", ctypes.c_int),
                 ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int),
-                ("restart", ctypes.c_int), ("spmv", ctypes.c_int), ("test_stall", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("spmv", ctypes.c_int), ("test_stall", ctypes.c_int),
+                ("block_kernel", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -39,7 +40,7 @@ class ls_info(ctypes.Structure):
                 ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int),
                 ("ms_local", ctypes.c_double), ("ms_spmv", ctypes.c_double), ("ms_coarse", ctypes.c_double),
                 ("local_launches", ctypes.c_int), ("launches", ctypes.c_int), ("ms_iter", ctypes.c_double),
-                ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int)]
+                ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int), ("local_kernel", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1347,6 +1347,7 @@ void ls_default_options(ls_options* o) {
   o->restart = 100;
   o->spmv = 0;
   o->test_stall = 0;
+  o->block_kernel = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1377,6 +1378,7 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.solver == 2 && (h->opt.restart < 1 || h->opt.restart > 1000))
       throw LsError(LS_ERR_INVALID, "restart must lie in [1, 1000]");
     if (h->opt.test_stall != 0 && h->opt.test_stall != 1) throw LsError(LS_ERR_INVALID, "test_stall must be 0 or 1");
+    if (h->opt.block_kernel < 0 || h->opt.block_kernel > 2) throw LsError(LS_ERR_INVALID, "block_kernel must be 0, 1 or 2");
     if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))
       throw LsError(LS_ERR_INVALID, "spmv must be 0 or a sparse-product kernel code");
     if (h->opt.variant != 0 && nprob > 1)

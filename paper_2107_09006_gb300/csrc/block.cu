@@ -56,19 +56,90 @@ void ensure_buffers(ls_handle* h, int R) {
   B.R0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   B.Y0.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
   if (B.ZT.p) B.Y0f.alloc(std::max<size_t>((size_t)h->n0 * R, 1));
-  if (B.use_tc && !B.Lsw.p) {
-    B.Lsw.alloc(h->fac_elems);
-    lsq::launch_b_swizzle(h->fac_elems, h->L32.p, B.Lsw.p, h->st);
-    check_launch("swizzled factor copy");
-  }
   B.R = R;
 }
 
-// z = M^{-1} r for all pairs, with the partials of r.z (and rold.z when flexible).
-void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool flex, bool timed) {
+// The update tiles of every block step of the right-looking sweeps (tcgen05 kernel) and
+// the copies they are read from, built from the solve storage at the first use.
+void umma_prepare(ls_handle* h) {
+  BlockState& B = h->blk;
+  if (B.Uf.p) return;
+  cudaStream_t st = h->st;
+  const int64_t NB = h->total_blocks;
+  std::vector<int64_t> boff((size_t)h->N + 1), poff((size_t)NB + 1);
+  std::vector<int32_t> tf((size_t)NB);
+  CK(cudaMemcpyAsync(boff.data(), h->blk_off.p, sizeof(int64_t) * boff.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(poff.data(), h->blk_poff.p, sizeof(int64_t) * poff.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(tf.data(), h->blk_tf.p, sizeof(int32_t) * tf.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int64_t> foff((size_t)NB + 1, 0), boff2((size_t)NB + 1, 0), fsrc, bsrc;
+  std::vector<int32_t> frow, brow;
+  for (int i = 0; i < h->N; ++i) {
+    const int64_t b0 = boff[i];
+    const int nb = (int)(boff[i + 1] - b0);
+    for (int b = 0; b < nb; ++b) {
+      // forward step b: L_jb for the rows j > b whose envelope reaches column tile b
+      foff[b0 + b] = (int64_t)frow.size();
+      for (int j = b + 1; j < nb && j < b + h->wmax; ++j)
+        if (tf[b0 + j] <= b) {
+          fsrc.push_back(poff[b0 + j] + (int64_t)(b - tf[b0 + j]) * 1024);
+          frow.push_back(j);
+        }
+      // backward step b: L_bt for the tile columns b > t >= tf_b of block row b
+      boff2[b0 + b] = (int64_t)brow.size();
+      for (int t = b - 1; t >= tf[b0 + b]; --t) {  // nearest row first: it is needed first
+        bsrc.push_back(poff[b0 + b] + (int64_t)(t - tf[b0 + b]) * 1024);
+        brow.push_back(t);
+      }
+    }
+  }
+  foff[NB] = (int64_t)frow.size();
+  boff2[NB] = (int64_t)brow.size();
+  B.uf_off.upload(foff, st);
+  B.ub_off.upload(boff2, st);
+  B.uf_row.upload(frow, st);
+  B.ub_row.upload(brow, st);
+  DevBuf<int64_t> fs, bs;
+  fs.upload(fsrc, st);
+  bs.upload(bsrc, st);
+  B.Uf.alloc(std::max<size_t>(frow.size(), 1) * 1024);
+  B.Ub.alloc(std::max<size_t>(brow.size(), 1) * 1024);
+  B.Ud.alloc((size_t)NB * 2 * 32 * 36);
+  lsq::launch_bu_copy((int64_t)frow.size(), fs.p, h->L32.p, B.Uf.p, 0, st);
+  lsq::launch_bu_copy((int64_t)brow.size(), bs.p, h->L32.p, B.Ub.p, 1, st);
+  lsq::launch_bu_diag(NB, h->blk_poff.p, h->L32.p, B.Ud.p, st);
+  CK(cudaStreamSynchronize(st));
+  check_launch("tcgen05 factor copies");
+}
+
+void swizzle_prepare(ls_handle* h) {
+  BlockState& B = h->blk;
+  if (B.Lsw.p) return;
+  B.Lsw.alloc(h->fac_elems);
+  lsq::launch_b_swizzle(h->fac_elems, h->L32.p, B.Lsw.p, h->st);
+  CK(cudaStreamSynchronize(h->st));
+  check_launch("swizzled factor copy");
+}
+
+void launch_local_kernel(ls_handle* h, int kernel, int R, const double* Rin) {
   BlockState& B = h->blk;
   cudaStream_t st = h->st;
-  if (timed) record_event(h->ev[2], st);
+  if (kernel == 2) {
+    lsq::BUmmaArgs u{};
+    u.N = h->N; u.order = B.order.p;
+    u.om_off = h->om_off.p; u.om_glob = h->om_glob.p; u.eqs = h->eqs.p; u.blk_off = h->blk_off.p;
+    u.ffac = B.Uf.p; u.f_off = B.uf_off.p; u.f_row = B.uf_row.p;
+    u.bfac = B.Ub.p; u.b_off = B.ub_off.p; u.b_row = B.ub_row.p;
+    u.dinv = B.Ud.p;
+    u.Rv = Rin; u.Y = B.Y.p; u.R = R;
+    u.spill = reinterpret_cast<float*>(B.Vg.p);
+    u.ring = B.u_ring; u.tmem_cols = B.u_tmem; u.fs = B.u_fs;
+    u.ncol = lsq::block_local_umma_ncol(std::max(h->wmax - 1, 1));
+    u.err = h->scal.p + lsq::S_ERR;
+    u.stall = h->opt.test_stall;
+    lsq::launch_b_local_umma(u, B.u_grid, st);
+    return;
+  }
   lsq::BLocalArgs a{};
   a.N = h->N; a.order = B.order.p; a.qctr = B.qctr.p;
   a.om_off = h->om_off.p; a.om_glob = h->om_glob.p; a.eqs = h->eqs.p;
@@ -79,13 +150,61 @@ void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool fl
   a.Rv = Rin; a.Y = B.Y.p; a.R = R; a.Vg = B.Vg.p; a.ring = B.ring;
   a.err = h->scal.p + lsq::S_ERR;
   a.stall = h->opt.test_stall;
-  if (B.use_tc) {
+  if (kernel == 1) {
     a.fac = B.Lsw.p;
     a.tsc = nullptr;
     lsq::launch_b_local_tc(a, B.local_grid, st);
   } else {
     lsq::launch_b_local(h->prec, a, B.local_grid, st);
   }
+}
+
+// FP32 factors: which tensor-core local solve this handle uses (option block_kernel, or
+// the faster of the two, timed once here, outside any stream capture, on the first
+// block apply's right-hand side).
+void choose_local_kernel(ls_handle* h, int R, const double* Rin) {
+  BlockState& B = h->blk;
+  if (B.kernel != 0 || !B.use_tc) return;
+  const int opt = h->opt.block_kernel;
+  if (opt == 2 && !B.u_ok)
+    throw LsError(LS_ERR_UNSUPPORTED, "the tcgen05 local solve does not fit this factor's widest block row");
+  if (opt == 1 || (!B.u_ok && opt == 0)) {
+    swizzle_prepare(h);
+    B.kernel = 1;
+    return;
+  }
+  umma_prepare(h);
+  if (opt == 2 || h->opt.test_stall) {
+    B.kernel = 2;
+    return;
+  }
+  swizzle_prepare(h);
+  cudaStream_t st = h->st;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms[3] = {0.f, 0.f, 0.f};
+  for (int k = 1; k <= 2; ++k) {
+    launch_local_kernel(h, k, R, Rin);  // warm-up
+    CK(cudaEventRecord(e0, st));
+    launch_local_kernel(h, k, R, Rin);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms[k], e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_launch("block local-solve timing");
+  B.kernel = ms[2] <= ms[1] ? 2 : 1;
+}
+
+// z = M^{-1} r for all pairs, with the partials of r.z (and rold.z when flexible).
+void precond_block(ls_handle* h, int R, const double* Rin, double* Zout, bool flex, bool timed) {
+  BlockState& B = h->blk;
+  cudaStream_t st = h->st;
+  choose_local_kernel(h, R, Rin);
+  if (timed) record_event(h->ev[2], st);
+  launch_local_kernel(h, B.use_tc ? B.kernel : 0, R, Rin);
   if (timed) record_event(h->ev[3], st);
   const bool coarse = h->coarse && h->n0 > 0;
   const bool zt = coarse && B.ZT.p != nullptr;
@@ -218,6 +337,18 @@ void block_plan(ls_handle* h) {
     B.local_grid = std::max(1, std::min(h->N, sms * std::max(occ, 1)));
     B.Vg.alloc((size_t)h->total_blocks * 1024 * arith_bytes(h->prec));
   }
+  if (B.use_tc) {
+    // tcgen05 kernel: a window of (widest block row + 1) tiles, one CTA per SM, tensor
+    // memory for the M = 128 chunks of the largest step (at most widest - 1 tiles)
+    B.u_ring = h->wmax + 1;
+    B.u_tmem = lsq::block_local_umma_tmem_cols(std::max(h->wmax - 1, 1));
+    B.u_fs = lsq::block_local_umma_stages(B.u_ring, (size_t)optin);
+    B.u_smem = lsq::block_local_umma_smem(B.u_ring, B.u_fs);
+    B.u_ok = B.local_ok && B.u_tmem > 0 && B.u_smem <= (size_t)optin && lsq::block_local_umma_prepare(B.u_smem);
+    B.u_grid = std::max(1, std::min(h->N, sms));
+    cudaGetLastError();
+  }
+  B.kernel = 0;
   // coarse tiles (problem, 32-row tile)
   std::vector<int32_t> cp, cr, n0q(h->nprob, 0);
   for (int q = 0; q < h->nprob; ++q) {
@@ -390,6 +521,7 @@ bool block_core(ls_handle* h, int R, double rtol, int mode, const std::vector<do
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  inf.local_kernel = h->blk.use_tc ? h->blk.kernel : 0;
   return converged || fixed > 0;
 }
 

@@ -125,6 +125,17 @@ struct BlockState {
   bool local_ok = false;  // the ring fits the shared memory of one CTA
   bool use_tc = false;    // FP32 factors: tensor-core local solves from the swizzled copy
   DevBuf<float> Lsw;      // TF32-rounded swizzled factor tiles (made at the first block solve)
+  // tcgen05 local solve (FP32 factors): per-step update tiles, the two TF32 copies in
+  // core-matrix layout and the padded inverse diagonal tiles (made at the first block
+  // solve that uses it); kernel: 1 the mma.sync kernel, 2 the tcgen05 kernel, 0 not yet
+  // chosen (option block_kernel, or timed once at the first block solve)
+  int kernel = 0;
+  bool u_ok = false;
+  int u_ring = 0, u_tmem = 0, u_grid = 0, u_fs = 0;
+  size_t u_smem = 0;
+  DevBuf<float> Uf, Ub, Ud;
+  DevBuf<int64_t> uf_off, ub_off;
+  DevBuf<int32_t> uf_row, ub_row;
   // coarse solve tiles: (problem, 32-row tile) pairs
   DevBuf<int32_t> ct_prob, ct_row, n0q;
   // mixed forms: FP32 transposed coarse basis and FP32 copy of the coarse solution

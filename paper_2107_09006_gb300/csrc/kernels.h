@@ -231,6 +231,43 @@ void launch_b_local(int prec, const BLocalArgs& a, int grid, cudaStream_t st);
 int block_local_tc_occupancy(int ring);
 void launch_b_local_tc(const BLocalArgs& a, int grid, cudaStream_t st);
 void launch_b_swizzle(int64_t nelem, const float* src, float* dst, cudaStream_t st);
+
+// FP32 factors on the 5th-generation tensor cores (tcgen05, k_block_umma.cu): right-
+// looking sweeps whose block-step updates run as M = 128 MMAs with the accumulator in
+// tensor memory.  f_* / b_*: the update tiles of the forward / backward step of global
+// block row g are [off[g], off[g + 1]) of the forward / backward copy (TF32, core-matrix
+// layout, 1024 floats per tile), row[e] the local block row tile e updates; dinv: the
+// inverse diagonal tile of every block row, row-major with rows of 33 floats.
+struct BUmmaArgs {
+  int N; const int32_t* order;                  // subdomains by decreasing size (dealt round-robin)
+  const int64_t* om_off; const int32_t* om_glob; const double* eqs;
+  const int64_t* blk_off;
+  const float* ffac; const int64_t* f_off; const int32_t* f_row;
+  const float* bfac; const int64_t* b_off; const int32_t* b_row;
+  const float* dinv;
+  const double* Rv; double* Y; int R;
+  float* spill;   // forward results of block rows that leave the window (1024 floats per block row)
+  int ring;       // window tiles kept in shared memory (>= widest block row + 1)
+  int tmem_cols;  // tensor-memory columns (512: two steps x 256)
+  int ncol;       // accumulator columns per chunk: 64 (steps of <= 4 chunks) or 32 (<= 8)
+  int fs;         // factor chunk stages (block_local_umma_stages)
+  double* err;
+  int stall;      // test hook: 1 issues no copies, so the bounded waits run out
+};
+size_t block_local_umma_smem(int ring, int fs);
+// the most factor chunk stages (2 .. 8) whose shared memory fits smem_limit
+int block_local_umma_stages(int ring, size_t smem_limit);
+// tensor-memory columns for steps of at most max_step_tiles update tiles (0: unsupported)
+int block_local_umma_tmem_cols(int max_step_tiles);
+// accumulator columns per chunk for such steps (64, or 32 for more than 4 chunks)
+int block_local_umma_ncol(int max_step_tiles);
+bool block_local_umma_prepare(size_t smem);
+void launch_b_local_umma(const BUmmaArgs& a, int grid, cudaStream_t st);
+// tile t of dst <- the 32 x 32 column-major tile at L32 + src_off[t], TF32-rounded, in
+// core-matrix layout (transpose: the tile's columns along M)
+void launch_bu_copy(int64_t ntiles, const int64_t* src_off, const float* L32, float* dst, int transpose,
+                    cudaStream_t st);
+void launch_bu_diag(int64_t nblocks, const int64_t* poff, const float* L32, float* dst, cudaStream_t st);
 void launch_b_spmm_csr(const CsrDev& A, const double* X, double* Y, int R, cudaStream_t st);
 void launch_b_spmm_csc(const BChunks& ch, const CscDev& At, const double* Q, double* W, int R, const double* D,
                        double* part, cudaStream_t st);

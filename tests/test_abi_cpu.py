@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_options(lib):
     o = lib.ls_default_options()
     assert (o.nev_max, o.delta_rel, o.s_rel, o.maxit, o.coarse, o.use_graph) == (16, 1e-10, 1e-8, 1000, 1, 1)
-    assert (o.variant, o.solver, o.restart, o.spmv, o.test_stall) == (0, 0, 100, 0, 0)
+    assert (o.variant, o.solver, o.restart, o.spmv, o.test_stall, o.block_kernel) == (0, 0, 100, 0, 0, 0)
 
 
 @pytest.mark.parametrize("which", ["tiny", "ragged", "example"])

@@ -248,3 +248,84 @@ def test_tf32_factor_error_stated(grid96):
     assert e_block <= 10 * e_model
     assert e_single * 20 <= e_model
     S.close()
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_block_kernels_first_iterate_and_convergence(grid96, kernel):
+    """Both tensor-core local solves of the FP32 block path (option block_kernel: 1 the
+    TF32 mma.sync kernel with left-looking sweeps, 2 the tcgen05 kernel with
+    right-looking sweeps and the accumulator in tensor memory): the first PCG iterate of
+    5 right-hand sides within 10x the TF32-rounded-factor model's error of the FP64
+    oracle, and every pair converged to 1e-10 within one iteration of the oracle's
+    count."""
+    import scipy.linalg as sl
+    d = grid96
+    A, M = d["A"], d["M"]
+
+    def apply_tf32(r):
+        z = np.zeros_like(r)
+        for idx, (c, lower) in M.local:
+            y = sl.cho_solve((_round_tf32(np.tril(c)), lower), r[idx])
+            np.add.at(z, idx, y)
+        return z + M.apply_coarse(r)
+
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16, factor_prec="f32",
+                 fixed_iters=1, block_kernel=kernel)
+    X, info = S.solve(d["b"], rtol=1e-8)
+    assert info["local_kernel"] == kernel
+    for k in range(5):
+        xo = O.pcg(A, d["b"][k], M.apply, fixed_iters=1)[0]
+        xm = O.pcg(A, d["b"][k], apply_tf32, fixed_iters=1)[0]
+        assert rel(X[k].cpu().numpy(), xo) <= 10 * rel(xm, xo), k
+    S.close()
+    S = L.Solver(d["m"], d["n"], d["rp"], d["c"], d["v"], d["part"], 9, nev_max=16, factor_prec="f32",
+                 block_kernel=kernel)
+    X, _ = S.solve(d["b"], rtol=1e-10)
+    its, relres = S.batch_stats(5)
+    assert (relres <= 1e-10).all()
+    for k in range(5):
+        _, io = O.pcg(A, d["b"][k], M.apply, rtol=1e-10)
+        assert abs(int(its[0, k]) - io["iters"]) <= 1, k
+    S.close()
+
+
+def test_tcgen05_kernel_matches_mma_sync_kernel(batch):
+    """On the batched problems (uneven subdomains, 3 right-hand sides: 29 of the 32
+    MMA columns are padding) both tensor-core kernels apply a TF32-rounded factor (the
+    mma.sync kernel also rounds the inverse diagonal tiles; the tcgen05 kernel applies
+    those in FP32): after 4 fixed iterations every problem's iterates lie within 10x the
+    TF32-rounded-factor model's error of the oracle's FP64 PCG, the two kernels agree to
+    1e-3 (each is within about 4e-4 of FP64), every converged pair meets its own test,
+    and the automatic choice picks one of the two."""
+    import scipy.linalg as sl
+    B, oracles = batch
+    R = 3
+    xs = {}
+    for kernel in (1, 2):
+        S = _batched(B, factor_prec="f32", fixed_iters=4, block_kernel=kernel)
+        X, info = S.solve(B.b, rtol=1e-8)
+        assert info["local_kernel"] == kernel
+        xs[kernel] = X.cpu().numpy()
+        S.close()
+        S = _batched(B, factor_prec="f32", block_kernel=kernel)
+        S.solve(B.b, rtol=1e-9)
+        its, relres = S.batch_stats(R)
+        assert (relres <= 1e-9).all(), kernel
+        S.close()
+    assert rel(xs[2], xs[1]) < 1e-3
+    for q, (A, M, b) in enumerate(oracles):
+        def apply_tf32(r, M=M):
+            z = np.zeros_like(r)
+            for idx, (c, lower) in M.local:
+                y = sl.cho_solve((_round_tf32(np.tril(c)), lower), r[idx])
+                np.add.at(z, idx, y)
+            return z + M.apply_coarse(r)
+        n0, n1 = int(B.n_off[q]), int(B.n_off[q + 1])
+        for k in range(R):
+            xo = O.pcg(A, b[k], M.apply, fixed_iters=4)[0]
+            xm = O.pcg(A, b[k], apply_tf32, fixed_iters=4)[0]
+            assert rel(xs[2][k, n0:n1], xo) <= 10 * rel(xm, xo), (q, k)
+    S = _batched(B, factor_prec="f32")
+    _, info = S.solve(B.b, rtol=1e-8)
+    assert info["local_kernel"] in (1, 2)
+    S.close()

@@ -45,13 +45,15 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     S2.close()
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_block_path_bounded_wait_reports_timeout(prec):
-    """The same on the multi right-hand-side path: the tensor-core kernel (FP32 factors)
-    and the CUDA-core kernel (FP64 factors)."""
+@pytest.mark.parametrize("prec,kernel", [("f32", 1), ("f32", 2), ("f64", 0)])
+def test_block_path_bounded_wait_reports_timeout(prec, kernel):
+    """The same on the multi right-hand-side path: the two tensor-core kernels (FP32
+    factors: TF32 mma.sync, and tcgen05 whose copy, MMA and compute roles all give up
+    together) and the CUDA-core kernel (FP64 factors)."""
     P = config_tiny()
     B = np.stack([P.b, np.random.default_rng(3).standard_normal(P.m)])
-    S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec, test_stall=1)
+    S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec, test_stall=1,
+                 block_kernel=kernel)
     t0 = time.time()
     with pytest.raises(L.LSError) as ex:
         S.solve(B, rtol=1e-8)
@@ -59,7 +61,8 @@ def test_block_path_bounded_wait_reports_timeout(prec):
     assert time.time() - t0 < 60.0
     S.close()
     torch.cuda.synchronize()
-    S2 = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec)
+    S2 = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec=prec,
+                  block_kernel=kernel)
     X, _ = S2.solve(B, rtol=1e-10)
     its, rel = S2.batch_stats(2)
     assert (rel <= 1e-10).all()
