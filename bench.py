@@ -69,6 +69,9 @@ def parse():
                          "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
     ap.add_argument("--spmv", type=int, default=0,
                     help="solve mode: force one sparse-product kernel code for A and A^T (0: autotuned)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="solve mode: run the iterations from the host, kernel by kernel (the same kernels; for "
+                         "profilers that do not list the kernels inside a conditional graph node)")
     ap.add_argument("--block-kernel", type=int, default=0,
                     help="batch mode: local-solve kernel of the FP32 block path (0 timed choice, 1 TF32 mma.sync, "
                          "2 tcgen05)")
@@ -317,7 +320,7 @@ def run_ours(args):
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
                    nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,
-                   solver=solver, spmv=args.spmv)
+                   solver=solver, spmv=args.spmv, use_graph=0 if args.no_graph else 1)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()

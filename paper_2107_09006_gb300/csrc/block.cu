@@ -196,6 +196,14 @@ void choose_local_kernel(ls_handle* h, int R, const double* Rin) {
   cudaEventDestroy(e1);
   check_launch("block local-solve timing");
   B.kernel = ms[2] <= ms[1] ? 2 : 1;
+  // the other kernel's factor copy is not needed any more
+  CK(cudaStreamSynchronize(st));
+  if (B.kernel == 2) {
+    B.Lsw.release();
+  } else {
+    B.Uf.release(); B.Ub.release(); B.Ud.release();
+    B.uf_off.release(); B.ub_off.release(); B.uf_row.release(); B.ub_row.release();
+  }
 }
 
 // z = M^{-1} r for all pairs, with the partials of r.z (and rold.z when flexible).
