@@ -62,9 +62,7 @@ constexpr long long kWaitCycles = 4000000000ll;  // about two seconds at GB300 c
 // buffers and the barriers, rounded up to 16 bytes (vector reads of v).
 template <class TA, int S>
 __host__ __device__ constexpr size_t v_offset() {
-  // (FP64 keeps a second reduction buffer: its diagonal products reduce twice per step)
-  return ((size_t)S * kStageBytes + (kWarps * 32 * (sizeof(TA) == 8 ? 2 : 1) + 64) * sizeof(TA) +
-          (S + 1) * sizeof(uint64_t) + 15) / 16 * 16;
+  return ((size_t)S * kStageBytes + (kWarps * 32 + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) + 15) / 16 * 16;
 }
 
 // Order of the chunks one CTA consumes: forward sweep, blocks ascending, each segment's
@@ -111,8 +109,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   TA* red = reinterpret_cast<TA*>(smem_raw + S * kStageBytes);
   TA* tv = red + kWarps * 32;
   TA* xv = tv + 32;
-  TA* red2 = xv + 32;  // FP64 only
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red2 + (kSplit ? kWarps * 32 : 0));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xv + 32);
   int* abort_flag = reinterpret_cast<int*>(bars + S);
   TA* v = reinterpret_cast<TA*>(smem_raw + v_offset<TA, S>());  // 16-byte aligned
 
@@ -262,13 +259,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
         __syncthreads();
         const TF* D = ch + (offw - lo) * kT;  // inverse tile, column-major
         const TA dsc = sc ? (TA)sc[offw >> 5] : (TA)1;
-        if (!kSplit && w == 0) {
+        if (w == 0) {
           TA s = 0;
 #pragma unroll
           for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
           tv[lane] = v[b * kT + lane] - s;
           __syncwarp();
-          {
+          if (!kSplit) {
             TA x0 = 0, x1 = 0;  // two FMA chains
 #pragma unroll 8
             for (int c = 0; c < kT; c += 2) {
@@ -279,25 +276,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           }
         }
         if (kSplit) {  // FP64: the 32x32 product spread over the warps (the FP64 pipe is narrow)
-          // warp w forms the entries 4w .. 4w+3 of v_b - L_off v_window itself (lanes 0-3)
-          // and shares them by shuffles; the partial products go to the second buffer
-          TA t = 0;
-          if (lane < 4) {
-            const int c = 4 * w + lane;
-            TA s = 0;
-#pragma unroll
-            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + c];
-            t = v[b * kT + c] - s;
-          }
+          // (the sums above stay on warp 0: FP64 additions with few active lanes would
+          // occupy the FP64 units like full-warp ones)
+          __syncthreads();
           TA x = 0;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) x += Val<TF>::f(D[(4 * w + j) * kT + lane]) * __shfl_sync(0xffffffffu, t, j);
-          red2[w * 32 + lane] = x;
+          for (int c = 4 * w; c < 4 * w + 4; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
+          red[w * 32 + lane] = x;
           __syncthreads();
           if (w == 0) {
             TA s = 0;
 #pragma unroll
-            for (int u = 0; u < kWarps; ++u) s += red2[u * 32 + lane];
+            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
             v[b * kT + lane] = s * dsc;
           }
         }
@@ -384,31 +374,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           vw[c] -= s;
         }
       } else {
-      // FP64: 8 columns per warp, 4 lanes per column (row group g = rows 4 i + g), the
-      // four partial sums of a column reduced by shuffles inside the warp; the rows are
-      // walked in an order rotated by column, which keeps the 64-bit reads of a
-      // half-warp on distinct banks
-      static_assert(CC == 8 * kWarps && G == 4 && RG == 8, "FP64 stage geometry");
-      const int cq = lane >> 2, g = lane & 3;
-      const int cl = w * 8 + cq;
+      // FP64: four row groups of 8 rows per column, their partial sums added by the
+      // first group through shared memory (fewer FP64 additions than a shuffle tree: the
+      // FP64 units are this kernel's bottleneck)
+      const int cl = tid % CC, g = tid / CC;
       const int c = lo + cl;
       TA s = 0;
       if (c < phi) {
-        const TF* col = ch + cl * kT;
+        const TF* col = ch + cl * kT + g * RG;
         TA s1 = 0;  // two FMA chains
 #pragma unroll
         for (int u = 0; u < RG; u += 2) {
-          const int r0 = 4 * ((u + cq) & 7) + g, r1 = 4 * ((u + 1 + cq) & 7) + g;
-          s += Val<TF>::f(col[r0]) * xv[r0];
-          s1 += Val<TF>::f(col[r1]) * xv[r1];
+          const int r0 = (u + c) & (RG - 1), r1 = (u + 1 + c) & (RG - 1);
+          s += Val<TF>::f(col[r0]) * xv[g * RG + r0];
+          s1 += Val<TF>::f(col[r1]) * xv[g * RG + r1];
         }
         s += s1;
-      }
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (g == 0 && c < phi) {
         if (sc) s *= (TA)sc[c >> 5];
-        vw[c] -= s;
+      }
+      red[g * CC + cl] = s;
+      __syncthreads();
+      if (g == 0 && c < phi) {
+        TA t = 0;
+#pragma unroll
+        for (int u = 0; u < G; ++u) t += red[u * CC + cl];
+        vw[c] -= t;
       }
       }
     }
