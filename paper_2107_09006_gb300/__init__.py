@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libls_schwarz.so")
+# LS_SCHWARZ_BOUNDS=1 loads the bounds-checked build (_build.build(debug_bounds=True)):
+# its kernels check their indices and report an out-of-range one as LS_ERR_INVALID
+_LIB_PATH = os.path.join(_HERE, "libls_schwarz_dbg.so" if os.environ.get("LS_SCHWARZ_BOUNDS") == "1"
+                         else "libls_schwarz.so")
 
 LS_OK, LS_ERR_INVALID, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_FACTOR, LS_ERR_EIGEN, LS_ERR_NOT_CONVERGED, \
     LS_ERR_NONFINITE, LS_ERR_DEVICE_TIMEOUT, LS_ERR_UNSUPPORTED = range(10)

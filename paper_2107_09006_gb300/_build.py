@@ -2,7 +2,10 @@
 
 Sources compile in parallel into ``_build/`` next to this file and link into
 ``libls_schwarz.so`` in the package directory.  A rebuild happens only when a
-source or header is newer than the library.
+source or header is newer than the library.  ``build(debug_bounds=True)`` makes the
+bounds-checked variant ``libls_schwarz_dbg.so`` (compiled with -DLS_DEBUG_BOUNDS into
+``_build_dbg/``): its gather, scatter and local-solve kernels check every index and copy
+range and report an out-of-range one as LS_ERR_INVALID instead of using it.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libls_schwarz.so")
+BUILD_DBG = os.path.join(HERE, "_build_dbg")
+LIB_DBG = os.path.join(HERE, "libls_schwarz_dbg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,25 +36,30 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every source for sm_103a and link the shared library; returns its path."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          debug_bounds: bool = False) -> str:
+    """Compile every source for sm_103a and link the shared library (the bounds-checked
+    variant with debug_bounds); returns its path."""
+    lib, bdir = (LIB_DBG, BUILD_DBG) if debug_bounds else (LIB, BUILD)
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH + (extra or [])
+    if debug_bounds:
+        flags.append("-DLS_DEBUG_BOUNDS")
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
@@ -61,13 +71,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared"] + ARCH + ["-o", tmp] + objs
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

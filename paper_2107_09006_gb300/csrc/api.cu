@@ -113,6 +113,7 @@ void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
   a.int_off = h->int_off.p; a.int_glob = h->int_glob.p; a.zoff = h->zoff.p; a.coff = h->coff.p;
   a.Z = h->Z.p; a.r0 = h->r0.p;
   a.stall = h->opt.test_stall;
+  a.n_cols = h->n; a.fac_elems = h->fac_elems;
   lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, h->st);
 }
 
@@ -123,6 +124,7 @@ void coarse_term(ls_handle* h, const double* v, double* out) {
   lsq::launch_gemv(h->n0p, h->Xinv.p, h->r0.p, h->y0.p, st);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.total_local = h->total_local; s.err = h->scal.p + lsq::S_ERR;
   s.coarse = 1; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
   s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p;
   s.z = out;
@@ -151,6 +153,7 @@ void precond_balanced(ls_handle* h, const double* rin, double* zout, bool dots, 
   if (timed) mark(h, 3);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.total_local = h->total_local; s.err = h->scal.p + lsq::S_ERR;
   s.z = h->bal_u.p;
   s.add_coarse_only = 2;
   lsq::launch_scatter(s, st);                                          // u = M_1 t
@@ -203,6 +206,7 @@ void precond(ls_handle* h, const double* rin, double* zout, int which, bool dots
   if (timed) mark(h, 4);
   lsq::ScatterArgs s{};
   s.n = h->n; s.map_ptr = h->map_ptr.p; s.map_idx = h->map_idx.p; s.y = h->ybuf.p;
+  s.total_local = h->total_local; s.err = h->scal.p + lsq::S_ERR;
   s.coarse = use_coarse ? 1 : 0; s.part = h->part.p; s.jj_of = h->jj_of.p; s.zoff = h->zoff.p;
   s.coff = h->coff.p; s.nI = h->nI.p; s.Z = h->Z.p; s.y0 = h->y0.p;
   s.r = rin; s.r_old = flex ? h->r_old.p : nullptr; s.z = zout;
@@ -443,6 +447,9 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
     it += done_now;
     inf.local_launches += done_now;
     rr = h->pin[lsq::S_RR];
+    if (h->pin[lsq::S_ERR] == lsq::kErrBounds)
+      throw LsError(LS_ERR_INVALID, "an index out of range was met (bounds-checked build) at iteration " +
+                                        std::to_string(it));
     if (h->pin[lsq::S_ERR] != 0.0)
       throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up at iteration " +
                                                std::to_string(it));

@@ -137,6 +137,7 @@ void launch_local_kernel(ls_handle* h, int kernel, int R, const double* Rin) {
     u.ncol = lsq::block_local_umma_ncol(std::max(h->wmax - 1, 1));
     u.err = h->scal.p + lsq::S_ERR;
     u.stall = h->opt.test_stall;
+    u.n_cols = h->n; u.f_tiles = (int64_t)(B.Uf.n / 1024); u.b_tiles = (int64_t)(B.Ub.n / 1024);
     lsq::launch_b_local_umma(u, B.u_grid, st);
     return;
   }
@@ -150,6 +151,7 @@ void launch_local_kernel(ls_handle* h, int kernel, int R, const double* Rin) {
   a.Rv = Rin; a.Y = B.Y.p; a.R = R; a.Vg = B.Vg.p; a.ring = B.ring;
   a.err = h->scal.p + lsq::S_ERR;
   a.stall = h->opt.test_stall;
+  a.n_cols = h->n;
   if (kernel == 1) {
     a.fac = B.Lsw.p;
     a.tsc = nullptr;
@@ -483,6 +485,9 @@ bool block_core(ls_handle* h, int R, double rtol, int mode, const std::vector<do
       inf.ms_spmv += ta; inf.ms_local += tb; inf.ms_coarse += tc; inf.ms_iter += td;
     }
     const double* perr = reinterpret_cast<const double*>(B.pin + 2);
+    if (*perr == lsq::kErrBounds)
+      throw LsError(LS_ERR_INVALID, "an index out of range was met (bounds-checked build) at iteration " +
+                                        std::to_string(it));
     if (*perr != 0.0)
       throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the block local-solve kernel gave up at iteration " +
                                                std::to_string(it));

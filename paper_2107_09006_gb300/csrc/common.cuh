@@ -4,11 +4,34 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "kernels.h"
+
 namespace lsq {
 
 constexpr int kThreads = 256;       // threads of every block-wide kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kT = 32;              // tile edge of the block-envelope storage
+
+// Bounds-checked build (-DLS_DEBUG_BOUNDS, the library libls_schwarz_dbg.so): the gather,
+// scatter and local-solve kernels check their indices and copy ranges; an index out of
+// range is not used: the kernel writes kErrBounds into the error slot it was given and
+// skips the access, and the host returns LS_ERR_INVALID.  In the product build every
+// check is a constant true.
+#ifdef LS_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, double* err) {
+  if constexpr (!kDebugBounds) {
+    return true;
+  } else {
+    if (i >= 0 && i < n) return true;
+    if (err) *err = kErrBounds;
+    return false;
+  }
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

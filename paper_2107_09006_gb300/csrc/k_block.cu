@@ -669,7 +669,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
       for (int e = tid; e < kT * kT; e += kThreads) {
         const int rr = e >> 5, k = e & 31, l = b * kT + rr;
         TA v = 0;
-        if (l < ni && k < R) v = (TA)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]);
+        if (l < ni && k < R && in_range(a.om_glob[o0 + l], a.n_cols, a.err))
+          v = (TA)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]);
         tin[e] = v;
       }
       __syncthreads();
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local(BLocalArgs a) {
   }
   if (sh[1]) {
     if (tid == 0) {
-      a.err[0] = 1.0;
+      if (a.err[0] == 0.0) a.err[0] = kErrTimeout;
       // bounded drain of the copies still in flight before the shared memory is released
       for (uint32_t qq = q; qq < issued; ++qq) {
         const long long t0 = clock64();
@@ -911,7 +912,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = tid + kThreads * u, rr = e >> 5, k = e & 31, l = b * kT + rr;
-        pre[u] = (l < ni && k < R) ? (float)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l]) : 0.f;
+        pre[u] = (l < ni && k < R && in_range(a.om_glob[o0 + l], a.n_cols, a.err))
+                     ? (float)(a.Rv[(int64_t)a.om_glob[o0 + l] * R + k] * a.eqs[o0 + l])
+                     : 0.f;
       }
     };
     fetch_rhs(0);
@@ -1043,7 +1046,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_b_local_tc(BLocalArgs a) {
   }
   if (sh[1]) {
     if (tid == 0) {
-      a.err[0] = 1.0;
+      if (a.err[0] == 0.0) a.err[0] = kErrTimeout;
       for (uint32_t qq = q; qq < issued; ++qq) {
         const long long c0 = clock64();
         while (!bar_try_wait(&bars[qq % S], (qq / S) & 1u))

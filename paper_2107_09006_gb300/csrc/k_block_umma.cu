@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(kUThreads, 1) k_b_local_umma(BUmmaArgs a) {
               continue;
             }
             const int64_t e0 = T.off[g], e1 = T.off[g + 1];
+            const int64_t ntl = sw == 0 ? a.f_tiles : a.b_tiles;
+            if (e1 > e0 && (!in_range(e0, ntl, a.err) || !in_range(e1 - 1, ntl, a.err))) {
+              ok = false;  // (bounds-checked build: a tile range outside the copy is not read)
+              break;
+            }
             for (int64_t e = e0; e < e1 && ok; e += kChunkTiles) {
               const int fs = (int)(q % FS);
               if (!mb_wait(&emptyb[fs], ((q / FS) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_b_local_umma(BUmmaArgs a) {
       }
       if (!ok) {
         *abort_flag = 1;
-        a.err[0] = 1.0;
+        if (a.err[0] == 0.0) a.err[0] = kErrTimeout;
       }
       // drain: every issued copy has landed before the CTA's shared memory goes away (a
       // landed copy's phase stays complete until its stage is refilled, which no longer
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_b_local_umma(BUmmaArgs a) {
       }
       if (!ok) {
         *abort_flag = 1;
-        a.err[0] = 1.0;
+        if (a.err[0] == 0.0) a.err[0] = kErrTimeout;
       }
       // every product issued has finished before tensor memory is released
       mma_commit(s.fin);
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_b_local_umma(BUmmaArgs a) {
           const int e = tid + 256 * u, r = e >> 5, n = e & 31, l = j * 32 + r;
           x.gi[u] = -1;
           x.sc[u] = 0.0;
-          if (j < nb && l < ni && n < R) {
+          if (j < nb && l < ni && n < R && in_range(a.om_glob[o0 + l], a.n_cols, a.err)) {
             x.gi[u] = a.om_glob[o0 + l];
             x.sc[u] = a.eqs[o0 + l];
           }
@@ -631,7 +636,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_b_local_umma(BUmmaArgs a) {
         }
       }
     }
-    if (!ok && tid == 0) a.err[0] = 1.0;
+    if (!ok && tid == 0 && a.err[0] == 0.0) a.err[0] = kErrTimeout;
   }
   tc_before();
   __syncthreads();

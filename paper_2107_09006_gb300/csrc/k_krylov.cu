@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(ScatterArgs a) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x) {
     double z = 0.0;
     if (a.add_coarse_only != 1) {
-      for (int64_t e = a.map_ptr[j]; e < a.map_ptr[j + 1]; ++e) z += a.y[a.map_idx[e]];
+      for (int64_t e = a.map_ptr[j]; e < a.map_ptr[j + 1]; ++e)
+        if (in_range(a.map_idx[e], a.total_local, a.err)) z += a.y[a.map_idx[e]];
     }
     if (a.coarse && a.add_coarse_only != 2) {
       const int i = a.part[j];

@@ -148,6 +148,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     const int hi = wd - prod.k * CC;
     const int lo = max(0, hi - CC);
     const uint32_t bytes = (uint32_t)((hi - lo) * kT * ES);
+    if (!in_range(poff[prod.b] + (int64_t)hi * kT - 1, a.fac_elems, a.err) || !in_range(poff[prod.b], a.fac_elems, a.err)) {
+      *abort_flag = 1;  // (bounds-checked build: the copy is not issued; its wait gives up)
+      prod.next();
+      ++issued;
+      return;
+    }
     fence_proxy_async();
     mbar_expect_tx(&bars[stage], bytes);
     bulk_g2s(ring + stage * CHUNK, fac + poff[prod.b] + (int64_t)lo * kT, bytes, &bars[stage]);
@@ -162,7 +168,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   }
   // gather r(Omega_i), scaled by the equilibration, while the first stages load
   for (int k = tid; k < nb * kT; k += blockDim.x)
-    v[k] = k < ni ? (TA)(a.r[a.om_glob[o0 + k]] * a.eqs[o0 + k]) : (TA)0;
+    v[k] = (k < ni && in_range(a.om_glob[o0 + k], a.n_cols, a.err)) ? (TA)(a.r[a.om_glob[o0 + k]] * a.eqs[o0 + k])
+                                                                     : (TA)0;
   if (a.coarse) {
     const int c0 = a.coff[i], kk = a.coff[i + 1] - c0;
     const int64_t io = a.int_off[i];
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   }
   if (*abort_flag) {
     if (issuer) {
-      a.err[0] = 1.0;
+      if (a.err[0] == 0.0) a.err[0] = kErrTimeout;
       // bounded drain of the copies still in flight before the CTA's shared memory is released
       for (int qq = q; qq < issued; ++qq) {
         const long long t0 = clock64();

@@ -25,6 +25,10 @@ struct CscDev {
 // warp; -2 sliced ELL.
 inline bool valid_spmv_code(int c) { return (c >= -3 && c <= -1) || c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
+// Values a kernel writes into the error slot it is given: a bounded wait gave up, or
+// (bounds-checked build) an index out of range was met and not used.
+constexpr double kErrTimeout = 1.0, kErrBounds = 3.0;
+
 // Scalar slots of the CG state kept on the device (copied to the host when the host
 // needs them).  S_THR: squared residual threshold (rtol ||g||)^2 of the device loop (0: no
 // test); S_ITS: iterations completed, written by the beta update.
@@ -82,6 +86,8 @@ struct ScatterArgs {
   double* z;
   DotSite dots;  // r.z -> out[0], r_old.z -> out[out2]; parts == nullptr: no dots
   int add_coarse_only;  // 1: z = coarse term only; 2: z = local sum only
+  int64_t total_local;  // entries of y (bounds-checked build)
+  double* err;          // error slot (bounds-checked build)
 };
 void launch_scatter(const ScatterArgs& a, cudaStream_t st);
 // One preconditioned LSQR step's vector updates: v = t / alpha, q = s / alpha, x += c1 w,
@@ -143,6 +149,7 @@ struct LocalArgs {
   const int32_t* coff; const double* Z; double* r0;
   double* err;  // set to 1 when a bounded wait on a copy gives up
   int stall;    // test hook: 1 issues no copies, so the bounded waits run out
+  int64_t n_cols, fac_elems;  // bounds of the gather indices and the factor (bounds-checked build)
 };
 size_t local_solve_smem(int prec, int max_nb);
 void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
@@ -222,6 +229,7 @@ struct BLocalArgs {
   int ring;  // tiles of the solution window kept in shared memory (>= widest block row)
   double* err;
   int stall;  // test hook: 1 issues no copies, so the bounded waits run out
+  int64_t n_cols;  // rows of Rv (bounds-checked build)
 };
 size_t block_local_smem(int fac_bytes, int arith_bytes, int ring);
 int block_local_occupancy(int prec, int ring);
@@ -253,6 +261,7 @@ struct BUmmaArgs {
   int fs;         // factor chunk stages (block_local_umma_stages)
   double* err;
   int stall;      // test hook: 1 issues no copies, so the bounded waits run out
+  int64_t n_cols, f_tiles, b_tiles;  // bounds of Rv and of the two copies (bounds-checked build)
 };
 size_t block_local_umma_smem(int ring, int fs);
 // the most factor chunk stages (2 .. 8) whose shared memory fits smem_limit

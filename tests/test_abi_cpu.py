@@ -143,3 +143,20 @@ def test_noalloc_binding_rejects_bad_arguments(lib):
         check(require_cuda=True)  # host tensors
     with pytest.raises(ValueError):
         lib.ls_normal_product_noalloc(m, n, *(good[k] for k in order[:6]), nnz, good["p"], good["w"])
+
+
+def test_bounds_checked_build_exports_the_same_symbols(lib):
+    """The bounds-checked variant (-DLS_DEBUG_BOUNDS, libls_schwarz_dbg.so) builds and
+    exports exactly the product library's symbols (its GPU behaviour is tested in
+    test_gpu_debug_bounds.py)."""
+    import ctypes
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_ls_build_t", os.path.join(ROOT, "paper_2107_09006_gb300",
+                                                                              "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = mod.build(debug_bounds=True)
+    assert os.path.basename(path) == "libls_schwarz_dbg.so"
+    so = ctypes.CDLL(path)
+    for name in lib.EXPORTED:
+        assert hasattr(so, name), name
