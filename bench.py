@@ -69,6 +69,11 @@ def parse():
                          "sum to zero: a Laplacian-like near null space that one-level Schwarz cannot handle)")
     ap.add_argument("--spmv", type=int, default=0,
                     help="solve mode: force one sparse-product kernel code for A and A^T (0: autotuned)")
+    ap.add_argument("--normal-product", type=int, default=0,
+                    help="solve mode: form of A^T (A p): 0 timed choice at setup, 1 two products, 2 row tiles")
+    ap.add_argument("--normal-kernel", type=int, default=0,
+                    help="solve mode: row-tile kernel configuration (0 timed choice, 1-3: 512 threads with that many "
+                         "slices per warp, 4: 1,024 threads)")
     ap.add_argument("--no-graph", action="store_true",
                     help="solve mode: run the iterations from the host, kernel by kernel (the same kernels; for "
                          "profilers that do not list the kernels inside a conditional graph node)")
@@ -172,6 +177,16 @@ def spmv_bytes(m: int, n: int, nnz: int) -> int:
     csr = nnz * 12 + (m + 1) * 8 + n * 8 + m * 8
     csc = nnz * 12 + (n + 1) * 8 + m * 8 + n * 8 + n * 8
     return csr + csc
+
+
+def tile_bytes(n: int, t: dict) -> int:
+    """Algorithmic bytes of the row-tile normal product (with the fused p.w): every stored
+    entry of both tile copies once (8-byte value, 2-byte index), the slice offsets and
+    column ids, the partial windows written and read back, p read once for the windows
+    and once for the dot, w written, and the per-tile and per-column-block tables."""
+    ent = (t["row_entries"] + t["col_entries"]) * 10
+    meta = (t["row_slices"] + t["col_slices"] + 2) * 8 + t["col_slices"] * 32 * 2 + t["tiles"] * 36 + (n // 256 + 1) * 8
+    return ent + meta + t["window_sum"] * 16 + n * 24
 
 
 def host_cores() -> dict:
@@ -320,7 +335,8 @@ def run_ours(args):
         t = time.time()
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
                    nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,
-                   solver=solver, spmv=args.spmv, use_graph=0 if args.no_graph else 1)
+                   solver=solver, spmv=args.spmv, use_graph=0 if args.no_graph else 1,
+                   normal_product=args.normal_product, normal_kernel=args.normal_kernel)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()
@@ -349,7 +365,8 @@ def run_ours(args):
         its = sum(i["iters"] for i in infos)
         ms_spmv = sum(i["ms_spmv"] for i in infos) / max(its, 1)
         lb = local_solve_bytes(st, form, restrict=variant == 0)
-        sb = spmv_bytes(P.m, P.n, P.nnz)
+        tiles = S.normal_tiles()
+        sb = tile_bytes(P.n, tiles) if infos[-1]["normal_product"] == 2 else spmv_bytes(P.m, P.n, P.nnz)
         loc_gbs = lb / (ms_local * 1e-3) / 1e9
         spmv_gbs = sb / (ms_spmv * 1e-3) / 1e9
         ms_iter = sum(i["ms_iter"] for i in infos) / max(its, 1)
@@ -359,7 +376,10 @@ def run_ours(args):
             "setup_s": setup_s, "eig_s": sinfo["t_eig"], "n0": sinfo["n0"], "kappa_lanczos": infos[-1]["kappa_lanczos"],
             "local_solve": {"ms_per_launch": ms_local, "bytes_per_launch": lb, "GBps": loc_gbs,
                             "frac": loc_gbs / hbm_peak, "share_of_step": nl * ms_local / (ms * args.steps)},
-            "spmv_pair": {"ms_per_iter": ms_spmv, "bytes_per_iter": sb, "GBps": spmv_gbs, "frac": spmv_gbs / hbm_peak},
+            "normal_product": {"form": "row tiles" if infos[-1]["normal_product"] == 2 else "two products",
+                               "tiles": tiles["tiles"], "kernel": tiles["kernel"], "setup_ms": tiles["setup_ms"],
+                               "ms_per_iter": ms_spmv, "bytes_per_iter": sb, "GBps": spmv_gbs,
+                               "frac": spmv_gbs / hbm_peak, "bytes_two_products": spmv_bytes(P.m, P.n, P.nnz)},
         }
         if headline:
             launches = sum(i["launches"] for i in infos)

@@ -114,6 +114,21 @@ typedef struct {
                           right-looking sweeps (LS_ERR_UNSUPPORTED if the widest factor
                           block row does not fit its shared-memory window).  Both round
                           the factor to TF32.  ls_info.local_kernel reports the choice. */
+    int normal_product;/* form of the product C v = A^T (A v): 0 (the default) times both
+                          at setup and keeps the faster (the two products alone when
+                          spmv forces a kernel); 1 two products, q = A v then A^T q; 2
+                          row tiles: A is cut into tiles of consecutive rows whose
+                          entries fall in a narrow column window, each tile forms A v
+                          for its rows and A^T of that for its window in shared memory
+                          from one tile-local copy, and the windows are summed per
+                          column in tile order (LS_ERR_UNSUPPORTED if one row's column
+                          span does not fit the shared memory of a block).  Both are
+                          bitwise repeatable.  ls_info.normal_product reports the form. */
+    int normal_kernel; /* row tiles: kernel configuration, 1, 2 or 3: blocks of 512
+                          threads whose warps take that many slices (of 32 rows or 32
+                          columns) at a time (more loads in flight, more registers); 4:
+                          blocks of 1,024 threads, one slice per warp; 0 (the default)
+                          times the four at setup.  Same results for all.            */
 } ls_options;
 
 typedef struct {
@@ -141,6 +156,7 @@ typedef struct {
     int local_kernel;        /* local-solve kernel of the last solve: 0 the single-vector or
                                 CUDA-core block kernel, 1 TF32 mma.sync block kernel, 2
                                 tcgen05 block kernel                                       */
+    int normal_product;      /* form of the A^T (A v) products: 1 two products, 2 row tiles */
 } ls_info;
 
 typedef struct ls_handle ls_handle;
@@ -149,7 +165,7 @@ typedef struct ls_handle ls_handle;
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
  * equilibrate = 0, variant = 0, solver = 0, restart = 100, spmv = 0, test_stall = 0,
- * block_kernel = 0. */
+ * block_kernel = 0, normal_product = 0, normal_kernel = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1, whose inputs are A, the subdomain count N and
@@ -275,9 +291,16 @@ typedef enum {
     LS_Q_STORAGE = 6,  /* int64[8]: factor elements (all subdomains), sum n_i, block
                           rows, coarse-basis elements, n0, padded n0, nnz(A), factor
                           precision (ls_precision)                                  */
-    LS_Q_BATCH = 7     /* float64[2 * nprob * nrhs] of the last multi right-hand-side
+    LS_Q_BATCH = 7,    /* float64[2 * nprob * nrhs] of the last multi right-hand-side
                           solve: iterations, then true relative residuals, each
                           indexed [problem * nrhs + rhs]                              */
+    LS_Q_NORMAL = 8    /* int64[12]: the row tiles of the normal product (the first seven
+                          0 when the two-product form runs): tiles, stored entries of
+                          the row copy and of the column copy (padding included), row
+                          slices, column slices, sum of the window widths, kernel
+                          configuration (option normal_kernel); then the setup timings
+                          behind the choice in ns per product (0: not timed): the two
+                          products, then configurations 1 to 4                       */
 } ls_query_kind;
 
 /* Copy one inspected array to the host buffer out (capacity cap elements of the

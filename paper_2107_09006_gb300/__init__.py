@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "libls_schwarz_dbg.so" if os.environ.get("LS_SCH
 LS_OK, LS_ERR_INVALID, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_FACTOR, LS_ERR_EIGEN, LS_ERR_NOT_CONVERGED, \
     LS_ERR_NONFINITE, LS_ERR_DEVICE_TIMEOUT, LS_ERR_UNSUPPORTED = range(10)
 LS_PREC_F64, LS_PREC_F32, LS_PREC_BF16 = 0, 1, 2
-LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH = range(8)
+LS_Q_SIZES, LS_Q_OMEGA, LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH, LS_Q_NORMAL = range(9)
 _PREC = {"f64": LS_PREC_F64, "f32": LS_PREC_F32, "bf16": LS_PREC_BF16}
 
 
@@ -32,7 +32,8 @@ class ls_options(ctypes.Structure):
                 ("eig_tol", ctypes.c_double), ("use_graph", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int),
                 ("restart", ctypes.c_int), ("spmv", ctypes.c_int), ("test_stall", ctypes.c_int),
-                ("block_kernel", ctypes.c_int)]
+                ("block_kernel", ctypes.c_int), ("normal_product", ctypes.c_int),
+                ("normal_kernel", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -43,7 +44,8 @@ class ls_info(ctypes.Structure):
                 ("t_solve", ctypes.c_double), ("bad_subdomain", ctypes.c_int), ("eig_steps_max", ctypes.c_int),
                 ("ms_local", ctypes.c_double), ("ms_spmv", ctypes.c_double), ("ms_coarse", ctypes.c_double),
                 ("local_launches", ctypes.c_int), ("launches", ctypes.c_int), ("ms_iter", ctypes.c_double),
-                ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int), ("local_kernel", ctypes.c_int)]
+                ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int), ("local_kernel", ctypes.c_int),
+                ("normal_product", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

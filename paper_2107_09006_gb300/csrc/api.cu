@@ -14,6 +14,7 @@
 
 #include "../../include/ls_schwarz.h"
 #include "host_sets.h"
+#include "normal_tiles.h"
 #include "kernels.h"
 
 namespace {
@@ -132,10 +133,21 @@ void coarse_term(ls_handle* h, const double* v, double* out) {
   lsq::launch_scatter(s, st);
 }
 
+// out = A^T (A v) in the form chosen at setup (two products, or the row tiles), with the
+// fused d . out into ds when ds.parts is set.
+void normal_product(ls_handle* h, const double* v, double* out, const double* d, const lsq::DotSite& ds,
+                    cudaStream_t st) {
+  if (h->normal_kind == 2) {
+    lsq::launch_normal_tiles(ntiles(h), v, out, d, ds, st);
+    return;
+  }
+  lsq::launch_spmv_csr(csr(h), v, h->q.p, h->lanes_csr, h->grid_csr, st);
+  lsq::launch_spmv_csc(csc(h), h->q.p, out, d, ds, h->lanes_csc, h->grid_csc, st);
+}
+
 // out = C v = A^T (A v)
 void apply_C(ls_handle* h, const double* v, double* out) {
-  lsq::launch_spmv_csr(csr(h), v, h->q.p, h->lanes_csr, h->grid_csr, h->st);
-  lsq::launch_spmv_csc(csc(h), h->q.p, out, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, h->st);
+  normal_product(h, v, out, nullptr, lsq::DotSite{}, h->st);
 }
 
 // Kernels of one apply of the balanced operator (see precond_balanced).
@@ -226,8 +238,7 @@ void iteration(ls_handle* h, bool flex, bool copy_scalars = true) {
   cudaStream_t st = h->st;
   const bool timed = h->opt.time_kernels != 0;
   if (timed) mark(h, 0);
-  lsq::launch_spmv_csr(csr(h), h->p.p, h->q.p, h->lanes_csr, h->grid_csr, st);
-  lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, h->p.p, site(h, lsq::S_PW, 0), h->lanes_csc, h->grid_csc, st);
+  normal_product(h, h->p.p, h->w.p, h->p.p, site(h, lsq::S_PW, 0), st);
   if (timed) mark(h, 1);
   lsq::launch_cg_update(h->n, h->scal.p, h->p.p, h->w.p, h->x.p, h->r.p, flex ? h->r_old.p : nullptr,
                         site(h, lsq::S_RR, 1), h->ctr.p, h->ahist.p, h->hist_cap, st);
@@ -489,7 +500,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.bad_subdomain = -1; inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.launches = launches;
-  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -530,7 +541,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
     inf.eig_steps_max = h->sinfo.eig_steps_max;
     inf.launches = launches;
-    inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+    inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
     inf.t_solve = now_s() - t0;
     if (info) *info = inf;
     if (!converged && h->opt.fixed_iters <= 0)
@@ -768,7 +779,7 @@ ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.launches = launches;
-  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -810,10 +821,26 @@ void refresh_value_copies(ls_handle* h) {
   lsq::launch_gather64(h->nnz, h->cperm.p, h->val.p, h->cval.p, st);
   lsq::launch_gather64((int64_t)h->sellA_src.n, h->sellA_src.p, h->val.p, h->sellA_val.p, st);
   lsq::launch_gather64((int64_t)h->sellB_src.n, h->sellB_src.p, h->val.p, h->sellB_val.p, st);
+  if (h->nt_tiles > 0) {
+    lsq::launch_gather64((int64_t)h->nt_asrc.n, h->nt_asrc.p, h->val.p, h->nt_aval.p, st);
+    lsq::launch_gather64((int64_t)h->nt_bsrc.n, h->nt_bsrc.p, h->val.p, h->nt_bval.p, st);
+  }
+}
+
+void release_normal_tiles(ls_handle* h) {
+  h->nt_tiles = 0;
+  h->nt_smem = 0;
+  h->nt_lo.release(); h->nt_wid.release(); h->nt_as0.release(); h->nt_bs0.release();
+  h->nt_aoff.release(); h->nt_acol.release(); h->nt_aval.release();
+  h->nt_boff.release(); h->nt_brow.release(); h->nt_bval.release(); h->nt_bcid.release();
+  h->nt_poff.release(); h->nt_asrc.release(); h->nt_bsrc.release();
+  h->nt_cb0.release(); h->nt_cb1.release(); h->nt_part.release();
 }
 
 // Lanes per row (A) and per column (A^T) of the two sparse products, picked by timing
-// every power of two on the actual matrix (three launches each, CUDA events).
+// every candidate kernel on the actual matrix (three launches each, CUDA events); then
+// the form of the normal product: the best pair against the row tiles (when built),
+// whose copies are freed if the pair wins.
 void autotune_spmv(ls_handle* h) {
   cudaStream_t st = h->st;
   DevBuf<double> xa, ya;
@@ -847,6 +874,44 @@ void autotune_spmv(ls_handle* h) {
     if (forced != 0 && lanes != forced) continue;
     const float ms = time_it([&] { lsq::launch_spmv_csc(csc(h), xa.p, ya.p, nullptr, lsq::DotSite{}, lanes, 0, st); });
     if (ms < best) { best = ms; h->lanes_csc = lanes; }
+  }
+  // The normal product runs after the local solve has streamed the factors through L2:
+  // its candidates are timed one launch at a time after a write of a buffer larger than L2.
+  h->normal_kind = 1;
+  if (h->nt_tiles > 0) {
+    DevBuf<unsigned char> flush;
+    flush.alloc((size_t)256 << 20);
+    auto time_cold = [&](auto&& launch) {
+      launch();  // warm
+      float total = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        CK(cudaMemsetAsync(flush.p, k, flush.n, st));
+        CK(cudaEventRecord(e0, st));
+        launch();
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        total += ms;
+      }
+      return total;
+    };
+    float best_tiles = 1e30f;
+    for (int cfg = 1; cfg <= 4; ++cfg) {
+      if (h->opt.normal_kernel != 0 && cfg != h->opt.normal_kernel) continue;
+      h->nt_cfg = cfg;
+      const float ms = time_cold([&] { lsq::launch_normal_tiles(ntiles(h), xa.p, ya.p, nullptr, lsq::DotSite{}, st); });
+      h->nt_ms[cfg] = ms / 3.f;
+      if (ms < best_tiles) { best_tiles = ms; best = (float)cfg; }
+    }
+    h->nt_cfg = (int)best;
+    const float pair = h->opt.normal_product == 2 ? 1e30f : time_cold([&] {
+      lsq::launch_spmv_csr(csr(h), xa.p, ya.p, h->lanes_csr, 0, st);
+      lsq::launch_spmv_csc(csc(h), ya.p, xa.p, nullptr, lsq::DotSite{}, h->lanes_csc, 0, st);
+    });
+    h->nt_ms[0] = h->opt.normal_product == 2 ? 0.f : pair / 3.f;
+    if (best_tiles < pair) h->normal_kind = 2;
+    else release_normal_tiles(h);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -949,6 +1014,31 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     h->sellB_off.upload(sb.off, st); h->sellB_perm.upload(sb.perm, st);
     h->sellB_col.upload(sb.col, st); h->sellB_val.upload(sb.val, st);
     CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  }
+  // row tiles of the one-pass normal product (a candidate unless a kernel is forced)
+  if (h->opt.normal_product == 2 || (h->opt.normal_product == 0 && h->opt.spmv == 0)) {
+    int smem_optin = 0;
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+    lsq::NormalTilesHost nt;
+    if (lsq::build_normal_tiles(h->m, h->n, hrp.data(), hcol.data(), hval.data(), smem_optin / 8 - 128, sms, nt)) {
+      h->nt_lo.upload(nt.lo, st); h->nt_wid.upload(nt.wid, st);
+      h->nt_as0.upload(nt.as0, st); h->nt_bs0.upload(nt.bs0, st);
+      h->nt_aoff.upload(nt.aoff, st); h->nt_acol.upload(nt.acol, st); h->nt_aval.upload(nt.aval, st);
+      h->nt_boff.upload(nt.boff, st); h->nt_brow.upload(nt.brow, st); h->nt_bval.upload(nt.bval, st);
+      h->nt_bcid.upload(nt.bcid, st); h->nt_poff.upload(nt.poff, st);
+      h->nt_asrc.upload(nt.asrc, st); h->nt_bsrc.upload(nt.bsrc, st);
+      h->nt_cb0.upload(nt.cb_t0, st); h->nt_cb1.upload(nt.cb_t1, st);
+      h->nt_part.alloc((size_t)nt.poff[nt.ntiles]);
+      h->nt_tiles = nt.ntiles;
+      h->nt_smem = nt.smem_doubles;
+      const int64_t st6[6] = {nt.ntiles, (int64_t)nt.aval.size(), (int64_t)nt.bval.size(), nt.as0[nt.ntiles],
+                              nt.bs0[nt.ntiles], nt.poff[nt.ntiles]};
+      for (int k = 0; k < 6; ++k) h->nt_stats[k] = st6[k];
+      CK(cudaStreamSynchronize(st));
+      if (!lsq::normal_tiles_prepare(ntiles(h))) release_normal_tiles(h);
+    }
+    if (h->nt_tiles == 0 && h->opt.normal_product == 2)
+      throw LsError(LS_ERR_UNSUPPORTED, "normal_product = 2: a row's column span does not fit a block's shared memory");
   }
   h->part.upload(hpart, st);
   autotune_spmv(h);
@@ -1305,6 +1395,9 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   CK(cudaStreamSynchronize(st));
   h->sinfo.t_setup = now_s() - t_begin;
   h->sinfo.bad_subdomain = -1;
+  h->sinfo.lanes_csr = h->lanes_csr;
+  h->sinfo.lanes_csc = h->lanes_csc;
+  h->sinfo.normal_product = h->normal_kind;
 }
 
 }  // namespace
@@ -1355,6 +1448,8 @@ void ls_default_options(ls_options* o) {
   o->spmv = 0;
   o->test_stall = 0;
   o->block_kernel = 0;
+  o->normal_product = 0;
+  o->normal_kernel = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1386,6 +1481,10 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
       throw LsError(LS_ERR_INVALID, "restart must lie in [1, 1000]");
     if (h->opt.test_stall != 0 && h->opt.test_stall != 1) throw LsError(LS_ERR_INVALID, "test_stall must be 0 or 1");
     if (h->opt.block_kernel < 0 || h->opt.block_kernel > 2) throw LsError(LS_ERR_INVALID, "block_kernel must be 0, 1 or 2");
+    if (h->opt.normal_product < 0 || h->opt.normal_product > 2)
+      throw LsError(LS_ERR_INVALID, "normal_product must be 0, 1 or 2");
+    if (h->opt.normal_kernel < 0 || h->opt.normal_kernel > 4)
+      throw LsError(LS_ERR_INVALID, "normal_kernel must lie in [0, 4]");
     if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))
       throw LsError(LS_ERR_INVALID, "spmv must be 0 or a sparse-product kernel code");
     if (h->opt.variant != 0 && nprob > 1)
@@ -1563,8 +1662,7 @@ ls_status ls_apply_normal(ls_handle* h, const double* p, double* w) {
     if (!h || !p || !w) throw LsError(LS_ERR_INVALID, "bad arguments");
     CK(cudaSetDevice(h->dev));
     CK(cudaMemcpyAsync(h->tv.p, p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
-    lsq::launch_spmv_csr(csr(h), h->tv.p, h->q.p, h->lanes_csr, h->grid_csr, h->st);
-    lsq::launch_spmv_csc(csc(h), h->q.p, h->w.p, nullptr, lsq::DotSite{}, h->lanes_csc, h->grid_csc, h->st);
+    normal_product(h, h->tv.p, h->w.p, nullptr, lsq::DotSite{}, h->st);
     CK(cudaMemcpyAsync(w, h->w.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     CK(cudaStreamSynchronize(h->st));
     check_launch("normal-equations product");
@@ -1597,6 +1695,14 @@ ls_status ls_query(const ls_handle* h, int kind, int i, void* out, int64_t cap) 
       for (int s = 0; s < N; ++s) zel += (int64_t)(h->h_k.empty() ? 0 : h->h_k[s]) * h->h_nI[s];
       o[0] = h->fac_elems; o[1] = h->total_local; o[2] = h->total_blocks; o[3] = zel;
       o[4] = h->n0; o[5] = h->n0p; o[6] = h->nnz; o[7] = h->prec;
+      return LS_OK;
+    }
+    if (kind == LS_Q_NORMAL) {
+      need(12);
+      int64_t* o = (int64_t*)out;
+      for (int k = 0; k < 6; ++k) o[k] = h->nt_tiles > 0 ? h->nt_stats[k] : 0;
+      o[6] = h->nt_tiles > 0 ? h->nt_cfg : 0;
+      for (int k = 0; k < 5; ++k) o[7 + k] = (int64_t)(h->nt_ms[k] * 1e6f);
       return LS_OK;
     }
     if (kind == LS_Q_BATCH) {

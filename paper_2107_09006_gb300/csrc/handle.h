@@ -176,6 +176,16 @@ struct ls_handle {
   DevBuf<int32_t> sellA_perm, sellA_col, sellB_perm, sellB_col;
   DevBuf<double> sellA_val, sellB_val;
   DevBuf<int64_t> cperm, sellA_src, sellB_src;  // source A' CSR slot of the CSC / ELL copies
+  // Row tiles of the one-pass normal product (normal_tiles.h); normal_kind: 1 two
+  // products, 2 row tiles (option normal_product, or timed at setup).
+  int normal_kind = 1;
+  int nt_tiles = 0, nt_smem = 0, nt_cfg = 2;
+  float nt_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // setup timings: the pair, then configurations 1-4
+  int64_t nt_stats[6] = {0, 0, 0, 0, 0, 0};  // LS_Q_NORMAL
+  DevBuf<int64_t> nt_lo, nt_aoff, nt_boff, nt_poff, nt_asrc, nt_bsrc;
+  DevBuf<int32_t> nt_wid, nt_as0, nt_bs0, nt_cb0, nt_cb1;
+  DevBuf<uint16_t> nt_acol, nt_brow, nt_bcid;
+  DevBuf<double> nt_aval, nt_bval, nt_part;
 
   DevBuf<int64_t> om_off, blk_off, blk_poff, map_ptr, map_idx, int_off;
   DevBuf<int32_t> om_glob, blk_tf, int_glob, int_loc, jj_of, nI;
@@ -257,6 +267,13 @@ inline lsq::CsrDev csr(const ls_handle* h) {
 inline lsq::CscDev csc(const ls_handle* h) {
   return lsq::CscDev{h->m, h->n, h->col_ptr.p, h->crow.p, h->cval.p,
                      lsq::SellDev{h->sellB.nslices, h->sellB_off.p, h->sellB_perm.p, h->sellB_col.p, h->sellB_val.p}};
+}
+
+inline lsq::NormalTilesDev ntiles(ls_handle* h) {
+  return lsq::NormalTilesDev{h->nt_tiles, h->nt_cfg, h->n, h->nt_smem, h->nt_lo.p, h->nt_wid.p, h->nt_as0.p, h->nt_bs0.p,
+                             h->nt_aoff.p, h->nt_acol.p, h->nt_aval.p, h->nt_boff.p, h->nt_brow.p, h->nt_bval.p,
+                             h->nt_bcid.p, h->nt_poff.p, h->nt_part.p, h->nt_cb0.p, h->nt_cb1.p,
+                             h->scal.p ? h->scal.p + lsq::S_ERR : nullptr};
 }
 
 // The multi right-hand-side PCG (block.cu): b [R][m] and x [R][n], host or device.

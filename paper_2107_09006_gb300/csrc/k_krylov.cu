@@ -8,6 +8,7 @@
 // bit-reproducible, and consumers read one scalar.
 #include "common.cuh"
 #include "kernels.h"
+#include "normal_tiles.h"
 
 namespace lsq {
 
@@ -432,6 +433,126 @@ __global__ void __launch_bounds__(kThreads) k_grad_vals(CsrDev A, const double* 
   }
 }
 
+// One-pass normal product, part 1: one block per row tile (layout in normal_tiles.h).
+// The tile's window of p is loaded into shared memory; each warp then takes row slices
+// (32 rows, lane l row l, entry k of every lane in one coalesced load) and leaves
+// s_j = a_j . p in shared memory; after a barrier each warp takes column slices (32
+// window columns) and forms u_c = sum_j a_jc s_j over the tile's rows, written over the p
+// window; the window goes to the tile's partial buffer.  Both sums run in storage
+// order.  The two sweeps read each stored entry once and gather only from shared memory.
+//
+// The sweeps are bound by the latency of the entry loads: a warp takes P adjacent slices
+// at a time and issues up to 8 entry loads of each before the first FMA, and it loads the
+// slice offsets of its next group while the current group's entries are in flight.
+// Configurations (option normal_kernel): 512 threads with P = 1, 2, 3, or 1,024 threads
+// with P = 1.
+
+// One sweep over slices [s_begin, s_end): acc = sum_k val[.] * src[idx[.]] per lane; the
+// result of slice s goes to dst[(s - s_begin) * 32 + lane] (cid == nullptr) or to
+// dst[cid[s * 32 + lane]] (lanes with cid 0xFFFF write nothing).
+template <int P, int NT>
+__device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, const uint16_t* __restrict__ idx,
+                                             const double* __restrict__ val, const uint16_t* __restrict__ cid,
+                                             int s_begin, int s_end, const double* src, int src_n, double* dst,
+                                             int dst_n, double* err) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31;
+  const int ng = (s_end - s_begin + P - 1) / P;
+  int64_t o[P + 1], no[P + 1];
+  auto load_off = [&](int g, int64_t(&oo)[P + 1]) {
+#pragma unroll
+    for (int q = 0; q <= P; ++q) oo[q] = __ldg(off + min(s_begin + g * P + q, s_end));
+  };
+  int g = threadIdx.x >> 5;
+  if (g < ng) load_off(g, o);
+  for (; g < ng; g += NW) {
+    int K[P], Kmax = 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      K[q] = (int)((o[q + 1] - o[q]) >> 5);
+      Kmax = max(Kmax, K[q]);
+    }
+    double acc[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) acc[q] = 0.0;
+    const bool more = g + NW < ng;
+    for (int k0 = 0; k0 < Kmax || k0 == 0; k0 += 8) {
+      int c[P][8];
+      double v[P][8];
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool ok = k0 + u < K[q];
+          const int64_t e = o[q] + lane + 32 * (k0 + u);
+          c[q][u] = ok ? (int)__ldg(idx + e) : 0;
+          v[q][u] = ok ? __ldg(val + e) : 0.0;
+        }
+      if (k0 == 0 && more) load_off(g + NW, no);
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (k0 + u < K[q] && in_range(c[q][u], src_n, err)) acc[q] = fma(v[q][u], src[c[q][u]], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int s = s_begin + g * P + q;
+      if (s >= s_end) break;
+      if (!cid) {
+        dst[(s - s_begin) * 32 + lane] = acc[q];
+      } else {
+        const int c = __ldg(cid + (int64_t)s * 32 + lane);
+        if (c != 0xFFFF && in_range(c, dst_n, err)) dst[c] = acc[q];
+      }
+    }
+    if (more) {
+#pragma unroll
+      for (int q = 0; q <= P; ++q) o[q] = no[q];
+    }
+  }
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 1) k_normal_tile(NormalTilesDev T, const double* __restrict__ p) {
+  extern __shared__ __align__(16) double nsm[];
+  const int t = blockIdx.x;
+  const int64_t lo = __ldg(T.lo + t);
+  const int W = __ldg(T.wid + t);
+  const int a0 = __ldg(T.as0 + t), a1 = __ldg(T.as0 + t + 1);
+  const int b0 = __ldg(T.bs0 + t), b1 = __ldg(T.bs0 + t + 1);
+  double* pw = nsm;
+  double* sv = nsm + ((W + 1) & ~1);
+  for (int i = threadIdx.x; i < W; i += NT) pw[i] = __ldg(p + lo + i);
+  __syncthreads();
+  normal_sweep<P, NT>(T.aoff, T.acol, T.aval, nullptr, a0, a1, pw, W, sv, (a1 - a0) * 32, T.err);
+  __syncthreads();
+  normal_sweep<P, NT>(T.boff, T.brow, T.bval, T.bcid, b0, b1, sv, (a1 - a0) * 32, pw, W, T.err);
+  __syncthreads();
+  double* out = T.part + __ldg(T.poff + t);
+  for (int i = threadIdx.x; i < W; i += NT) out[i] = pw[i];
+}
+
+// Part 2: w_c = sum of the partial windows that hold column c, in tile order (the tiles
+// to look at come from the table of each block of kNormalColBlock columns), with the
+// fused d . w.
+__global__ void __launch_bounds__(kThreads) k_normal_reduce(NormalTilesDev T, double* __restrict__ w,
+                                                            const double* __restrict__ d, DotSite ds) {
+  double dacc = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < T.n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = c / kNormalColBlock;
+    const int t0 = __ldg(T.cb_t0 + b), t1 = __ldg(T.cb_t1 + b);
+    double acc = 0.0;
+    for (int t = t0; t <= t1; ++t) {
+      const int64_t off = c - __ldg(T.lo + t);
+      if (off >= 0 && off < __ldg(T.wid + t)) acc += T.part[__ldg(T.poff + t) + off];
+    }
+    w[c] = acc;
+    dacc += (d ? d[c] : acc) * acc;
+  }
+  if (ds.parts) finish_dots(dacc, 0.0, false, ds);
+}
+
 int grid_for(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -488,6 +609,34 @@ void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double*
     case 16: k_spmv_csc<16><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
     default: k_spmv_csc<32><<<grid, kThreads, 0, st>>>(At, q, w, d, ds); break;
   }
+}
+
+bool normal_tiles_prepare(const NormalTilesDev& T) {
+  const size_t bytes = (size_t)T.smem_doubles * sizeof(double);
+  int dev = 0, cap = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  if (bytes > (size_t)cap) return false;
+  // the device's limit, not this matrix's need: handles of other matrices share the kernels
+  const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  return cudaFuncSetAttribute(k_normal_tile<1, 512>, a, cap) == cudaSuccess &&
+         cudaFuncSetAttribute(k_normal_tile<2, 512>, a, cap) == cudaSuccess &&
+         cudaFuncSetAttribute(k_normal_tile<3, 512>, a, cap) == cudaSuccess &&
+         cudaFuncSetAttribute(k_normal_tile<1, 1024>, a, cap) == cudaSuccess;
+}
+
+void launch_normal_tiles(const NormalTilesDev& T, const double* v, double* w, const double* d, const DotSite& ds,
+                         cudaStream_t st) {
+  const size_t smem = (size_t)T.smem_doubles * sizeof(double);
+  if (T.ntiles > 0) {
+    switch (T.config) {
+      case 2: k_normal_tile<2, 512><<<T.ntiles, 512, smem, st>>>(T, v); break;
+      case 3: k_normal_tile<3, 512><<<T.ntiles, 512, smem, st>>>(T, v); break;
+      case 4: k_normal_tile<1, 1024><<<T.ntiles, 1024, smem, st>>>(T, v); break;
+      default: k_normal_tile<1, 512><<<T.ntiles, 512, smem, st>>>(T, v); break;
+    }
+  }
+  k_normal_reduce<<<grid_for(T.n, kThreads, kVecGrid), kThreads, 0, st>>>(T, w, d, ds);
 }
 
 void launch_cg_update(int64_t n, double* scal, const double* p, const double* w, double* x, double* r, double* r_old,

@@ -48,6 +48,26 @@ void launch_spmv_csr(const CsrDev& A, const double* x, double* y, int lanes, int
 // w = A^T q; with ds.parts != nullptr also (d . w) -> *ds.out (d = w if d == nullptr).
 void launch_spmv_csc(const CscDev& At, const double* q, double* w, const double* d, const DotSite& ds, int lanes,
                      int grid, cudaStream_t st);
+// Row tiles of A for the one-pass normal product w = A^T (A p) (layout: normal_tiles.h).
+struct NormalTilesDev {
+  int ntiles;
+  int config;  // kernel configuration: 1, 2, 3 (512 threads, slices a warp takes at a time), 4 (1,024 threads)
+  int64_t n;
+  int smem_doubles;
+  const int64_t* lo; const int32_t* wid; const int32_t* as0; const int32_t* bs0;
+  const int64_t* aoff; const uint16_t* acol; const double* aval;
+  const int64_t* boff; const uint16_t* brow; const double* bval; const uint16_t* bcid;
+  const int64_t* poff; double* part;
+  const int32_t* cb_t0; const int32_t* cb_t1;
+  double* err;  // error slot (bounds-checked build)
+};
+// w = A^T (A v) over the row tiles (two launches: the tiles, then the per-column sum of
+// their partial windows in tile order, with the fused d . w as in launch_spmv_csc).
+void launch_normal_tiles(const NormalTilesDev& T, const double* v, double* w, const double* d, const DotSite& ds,
+                         cudaStream_t st);
+// Shared memory of the tile kernel for T (sets the kernel's limit; false if above the device's).
+bool normal_tiles_prepare(const NormalTilesDev& T);
+
 // alpha = scal[S_RZ] / scal[S_PW]; x += alpha p; r_old = r (if given); r -= alpha w; r.r -> rr.
 void launch_cg_update(int64_t n, double* scal, const double* p, const double* w, double* x, double* r,
                       double* r_old, const DotSite& rr, int* ctr, double* alpha_hist, int hist_cap,

@@ -8,7 +8,7 @@ import torch
 
 from . import (ls_setup, ls_setup_batched, ls_solve, ls_backward, ls_free, ls_default_options, ls_handle_info,
                ls_update_values, ls_apply_preconditioner, ls_apply_normal, ls_query, LS_Q_SIZES, LS_Q_OMEGA,
-               LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH)
+               LS_Q_XI, LS_Q_EIGVALS, LS_Q_ZBAR, LS_Q_EIGSTEPS, LS_Q_STORAGE, LS_Q_BATCH, LS_Q_NORMAL)
 
 
 def _dev(a, dtype, device):
@@ -147,6 +147,14 @@ class Solver:
         o = ls_query(self.h, LS_Q_STORAGE, 0, np.zeros(8, np.int64))
         keys = ("fac_elems", "total_local", "total_blocks", "zbar_elems", "n0", "n0_padded", "nnz", "prec")
         return {k: int(v) for k, v in zip(keys, o)}
+
+    def normal_tiles(self) -> dict:
+        """Layout of the row tiles of the normal product (zeros for the two-product form)."""
+        o = ls_query(self.h, LS_Q_NORMAL, 0, np.zeros(12, np.int64))
+        keys = ("tiles", "row_entries", "col_entries", "row_slices", "col_slices", "window_sum", "kernel")
+        d = {k: int(v) for k, v in zip(keys, o)}
+        d["setup_ms"] = {"two_products": o[7] * 1e-6, **{f"kernel_{c}": o[7 + c] * 1e-6 for c in range(1, 5)}}
+        return d
 
     def eig_steps(self) -> np.ndarray:
         return ls_query(self.h, LS_Q_EIGSTEPS, 0, np.zeros(self.nparts, np.int32))
