@@ -445,7 +445,9 @@ __global__ void __launch_bounds__(kThreads) k_grad_vals(CsrDev A, const double* 
 // at a time and issues up to 8 entry loads of each before the first FMA, and it loads the
 // slice offsets of its next group while the current group's entries are in flight.
 // Configurations (option normal_kernel): 512 threads with P = 1, 2, 3, or 1,024 threads
-// with P = 1.
+// with P = 1.  Slices are stored heaviest first; each warp starts on the group of its
+// index and then claims the next unclaimed group from a shared counter, so the warps
+// of a sweep finish close together.
 
 // One sweep over slices [s_begin, s_end): acc = sum_k val[.] * src[idx[.]] per lane; the
 // result of slice s goes to dst[(s - s_begin) * 32 + lane] (cid == nullptr) or to
@@ -454,8 +456,7 @@ template <int P, int NT>
 __device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, const uint16_t* __restrict__ idx,
                                              const double* __restrict__ val, const uint16_t* __restrict__ cid,
                                              int s_begin, int s_end, const double* src, int src_n, double* dst,
-                                             int dst_n, double* err) {
-  constexpr int NW = NT / 32;
+                                             int dst_n, int* claim, double* err) {
   const int lane = threadIdx.x & 31;
   const int ng = (s_end - s_begin + P - 1) / P;
   int64_t o[P + 1], no[P + 1];
@@ -465,7 +466,10 @@ __device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, co
   };
   int g = threadIdx.x >> 5;
   if (g < ng) load_off(g, o);
-  for (; g < ng; g += NW) {
+  while (g < ng) {
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(claim, 1);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
     int K[P], Kmax = 0;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -475,7 +479,7 @@ __device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, co
     double acc[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) acc[q] = 0.0;
-    const bool more = g + NW < ng;
+    const bool more = nxt < ng;
     for (int k0 = 0; k0 < Kmax || k0 == 0; k0 += 8) {
       int c[P][8];
       double v[P][8];
@@ -488,7 +492,7 @@ __device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, co
           c[q][u] = ok ? (int)__ldg(idx + e) : 0;
           v[q][u] = ok ? __ldg(val + e) : 0.0;
         }
-      if (k0 == 0 && more) load_off(g + NW, no);
+      if (k0 == 0 && more) load_off(nxt, no);
 #pragma unroll
       for (int q = 0; q < P; ++q)
 #pragma unroll
@@ -510,13 +514,16 @@ __device__ __forceinline__ void normal_sweep(const int64_t* __restrict__ off, co
 #pragma unroll
       for (int q = 0; q <= P; ++q) o[q] = no[q];
     }
+    g = nxt;
   }
 }
 
 template <int P, int NT>
 __global__ void __launch_bounds__(NT, 1) k_normal_tile(NormalTilesDev T, const double* __restrict__ p) {
   extern __shared__ __align__(16) double nsm[];
+  __shared__ int claim[2];
   const int t = blockIdx.x;
+  if (threadIdx.x == 0) claim[0] = claim[1] = NT / 32;
   const int64_t lo = __ldg(T.lo + t);
   const int W = __ldg(T.wid + t);
   const int a0 = __ldg(T.as0 + t), a1 = __ldg(T.as0 + t + 1);
@@ -525,9 +532,9 @@ __global__ void __launch_bounds__(NT, 1) k_normal_tile(NormalTilesDev T, const d
   double* sv = nsm + ((W + 1) & ~1);
   for (int i = threadIdx.x; i < W; i += NT) pw[i] = __ldg(p + lo + i);
   __syncthreads();
-  normal_sweep<P, NT>(T.aoff, T.acol, T.aval, nullptr, a0, a1, pw, W, sv, (a1 - a0) * 32, T.err);
+  normal_sweep<P, NT>(T.aoff, T.acol, T.aval, nullptr, a0, a1, pw, W, sv, (a1 - a0) * 32, claim, T.err);
   __syncthreads();
-  normal_sweep<P, NT>(T.boff, T.brow, T.bval, T.bcid, b0, b1, sv, (a1 - a0) * 32, pw, W, T.err);
+  normal_sweep<P, NT>(T.boff, T.brow, T.bval, T.bcid, b0, b1, sv, (a1 - a0) * 32, pw, W, claim + 1, T.err);
   __syncthreads();
   double* out = T.part + __ldg(T.poff + t);
   for (int i = threadIdx.x; i < W; i += NT) out[i] = pw[i];
@@ -616,13 +623,19 @@ bool normal_tiles_prepare(const NormalTilesDev& T) {
   int dev = 0, cap = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-  if (bytes > (size_t)cap) return false;
-  // the device's limit, not this matrix's need: handles of other matrices share the kernels
-  const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  return cudaFuncSetAttribute(k_normal_tile<1, 512>, a, cap) == cudaSuccess &&
-         cudaFuncSetAttribute(k_normal_tile<2, 512>, a, cap) == cudaSuccess &&
-         cudaFuncSetAttribute(k_normal_tile<3, 512>, a, cap) == cudaSuccess &&
-         cudaFuncSetAttribute(k_normal_tile<1, 1024>, a, cap) == cudaSuccess;
+  // Each configuration's limit is the device's (less its static shared memory), not this
+  // matrix's need: handles of other matrices share the kernels.
+  auto allow = [&](const void* fn) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return false;
+    const int dyn = cap - (int)fa.sharedSizeBytes;
+    if (bytes > (size_t)dyn) return false;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
+  };
+  const bool ok = allow((const void*)k_normal_tile<1, 512>) && allow((const void*)k_normal_tile<2, 512>) &&
+                  allow((const void*)k_normal_tile<3, 512>) && allow((const void*)k_normal_tile<1, 1024>);
+  if (!ok) cudaGetLastError();  // a refused setting leaves no error behind: the two products run instead
+  return ok;
 }
 
 void launch_normal_tiles(const NormalTilesDev& T, const double* v, double* w, const double* d, const DotSite& ds,
