@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--normal-kernel", type=int, default=0,
                     help="solve mode: row-tile kernel configuration (0 timed choice, 1-3: 512 threads with that many "
                          "slices per warp, 4: 1,024 threads)")
+    ap.add_argument("--local-config", type=int, default=0,
+                    help="solve mode: local-solve configuration (0 timed choice at setup, 1 256 threads / 16 KB "
+                         "stages, 2 512 threads / 32 KB stages)")
     ap.add_argument("--no-graph", action="store_true",
                     help="solve mode: run the iterations from the host, kernel by kernel (the same kernels; for "
                          "profilers that do not list the kernels inside a conditional graph node)")
@@ -336,7 +339,8 @@ def run_ours(args):
         S = Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, device=dev, stream=stream,
                    nev_max=args.nev, factor_prec=form, time_kernels=1, maxit=2000, variant=variant,
                    solver=solver, spmv=args.spmv, use_graph=0 if args.no_graph else 1,
-                   normal_product=args.normal_product, normal_kernel=args.normal_kernel)
+                   normal_product=args.normal_product, normal_kernel=args.normal_kernel,
+                   local_config=args.local_config)
         torch.cuda.synchronize(dev)
         setup_s = time.time() - t
         sinfo = S.info()
@@ -374,7 +378,7 @@ def run_ours(args):
             "value": ms / 1000.0, "iterations": infos[-1]["iters"], "relres_true": infos[-1]["relres_true"],
             "ms_per_iteration_kernels": ms_iter, "lanes": [infos[-1]["lanes_csr"], infos[-1]["lanes_csc"]],
             "setup_s": setup_s, "eig_s": sinfo["t_eig"], "n0": sinfo["n0"], "kappa_lanczos": infos[-1]["kappa_lanczos"],
-            "local_solve": {"ms_per_launch": ms_local, "bytes_per_launch": lb, "GBps": loc_gbs,
+            "local_solve": {"config": infos[-1]["local_config"], "ms_per_launch": ms_local, "bytes_per_launch": lb, "GBps": loc_gbs,
                             "frac": loc_gbs / hbm_peak, "share_of_step": nl * ms_local / (ms * args.steps)},
             "normal_product": {"form": "row tiles" if infos[-1]["normal_product"] == 2 else "two products",
                                "tiles": tiles["tiles"], "kernel": tiles["kernel"], "setup_ms": tiles["setup_ms"],

@@ -129,6 +129,12 @@ typedef struct {
                           columns) at a time (more loads in flight, more registers); 4:
                           blocks of 1,024 threads, one slice per warp; 0 (the default)
                           times the four at setup.  Same results for all.            */
+    int local_config;  /* single-vector local solve: 1 blocks of 256 threads with 16 KB
+                          stages, two per SM (many subdomains); 2 blocks of 512 threads
+                          with 32 KB stages, one per SM (subdomains that each get an SM:
+                          twice the warps, twice the columns per stage); 0 (the default)
+                          times both at the end of setup when both fit the shared
+                          memory and keeps the faster.  ls_info.local_config reports it. */
 } ls_options;
 
 typedef struct {
@@ -157,6 +163,7 @@ typedef struct {
                                 CUDA-core block kernel, 1 TF32 mma.sync block kernel, 2
                                 tcgen05 block kernel                                       */
     int normal_product;      /* form of the A^T (A v) products: 1 two products, 2 row tiles */
+    int local_config;        /* configuration of the single-vector local solve (option)      */
 } ls_info;
 
 typedef struct ls_handle ls_handle;
@@ -165,7 +172,7 @@ typedef struct ls_handle ls_handle;
  * s_rel = 1e-8, factor_prec = LS_PREC_F64, maxit = 1000, coarse = 1,
  * fixed_iters = 0, eig_maxit = 3000, eig_tol = 1e-11, use_graph = 1, time_kernels = 0,
  * equilibrate = 0, variant = 0, solver = 0, restart = 100, spmv = 0, test_stall = 0,
- * block_kernel = 0, normal_product = 0, normal_kernel = 0. */
+ * block_kernel = 0, normal_product = 0, normal_kernel = 0, local_config = 0. */
 void ls_default_options(ls_options* opt);
 
 /* Build the preconditioner (Algorithm 1, whose inputs are A, the subdomain count N and

@@ -33,7 +33,7 @@ class ls_options(ctypes.Structure):
                 ("equilibrate", ctypes.c_int), ("variant", ctypes.c_int), ("solver", ctypes.c_int),
                 ("restart", ctypes.c_int), ("spmv", ctypes.c_int), ("test_stall", ctypes.c_int),
                 ("block_kernel", ctypes.c_int), ("normal_product", ctypes.c_int),
-                ("normal_kernel", ctypes.c_int)]
+                ("normal_kernel", ctypes.c_int), ("local_config", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -45,7 +45,7 @@ class ls_info(ctypes.Structure):
                 ("ms_local", ctypes.c_double), ("ms_spmv", ctypes.c_double), ("ms_coarse", ctypes.c_double),
                 ("local_launches", ctypes.c_int), ("launches", ctypes.c_int), ("ms_iter", ctypes.c_double),
                 ("lanes_csr", ctypes.c_int), ("lanes_csc", ctypes.c_int), ("local_kernel", ctypes.c_int),
-                ("normal_product", ctypes.c_int)]
+                ("normal_product", ctypes.c_int), ("local_config", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

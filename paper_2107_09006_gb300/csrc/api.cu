@@ -115,7 +115,37 @@ void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
   a.Z = h->Z.p; a.r0 = h->r0.p;
   a.stall = h->opt.test_stall;
   a.n_cols = h->n; a.fac_elems = h->fac_elems;
-  lsq::launch_local_solve(h->prec, h->N, h->max_nb, a, h->st);
+  lsq::launch_local_solve(h->prec, h->local_cfg, h->N, h->max_nb, a, h->st);
+}
+
+// The local-solve configuration: forced by the option, else both timed on the factors
+// (two launches each after a warm one) when both fit the shared memory.
+void choose_local_config(ls_handle* h, int optin) {
+  h->local_cfg = 1;
+  const bool fat_fits = lsq::local_solve_smem(h->prec, h->max_nb, 2) <= (size_t)optin;
+  if (h->opt.local_config == 2) {
+    if (!fat_fits) throw LsError(LS_ERR_UNSUPPORTED, "local_config = 2: the largest subdomain does not fit");
+    h->local_cfg = 2;
+    return;
+  }
+  if (h->opt.local_config == 1 || !fat_fits || h->opt.test_stall) return;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms[3] = {0.f, 0.f, 0.f};
+  for (int cfg = 1; cfg <= 2; ++cfg) {
+    h->local_cfg = cfg;
+    launch_local(h, h->r.p, false);
+    CK(cudaEventRecord(e0, h->st));
+    for (int k = 0; k < 2; ++k) launch_local(h, h->r.p, false);
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms[cfg], e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_launch("local-solve configuration timing");
+  h->local_cfg = ms[2] < ms[1] ? 2 : 1;
 }
 
 // out = Q v = R_0^T C_00^{-1} R_0 v (restriction, dense coarse solve, prolongation)
@@ -500,7 +530,7 @@ ls_status solve_core(ls_handle* h, int mode, double rtol, ls_info* info) {
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.bad_subdomain = -1; inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.launches = launches;
-  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind; inf.local_config = h->local_cfg;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -541,7 +571,7 @@ ls_status lsqr_core(ls_handle* h, double rtol, ls_info* info) {
     inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
     inf.eig_steps_max = h->sinfo.eig_steps_max;
     inf.launches = launches;
-    inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
+    inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind; inf.local_config = h->local_cfg;
     inf.t_solve = now_s() - t0;
     if (info) *info = inf;
     if (!converged && h->opt.fixed_iters <= 0)
@@ -779,7 +809,7 @@ ls_status gmres_core(ls_handle* h, double rtol, ls_info* info) {
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.eig_steps_max = h->sinfo.eig_steps_max;
   inf.launches = launches;
-  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind; inf.local_config = h->local_cfg;
   inf.t_solve = now_s() - t0;
   if (info) *info = inf;
   if (!converged && fixed <= 0)
@@ -1057,7 +1087,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     // the local solve keeps one subdomain's right-hand side in shared memory
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-    const size_t need = lsq::local_solve_smem(h->opt.factor_prec, h->max_nb);
+    const size_t need = lsq::local_solve_smem(h->opt.factor_prec, h->max_nb, 1);
     if (need > (size_t)optin)
       throw LsError(LS_ERR_UNSUPPORTED, "largest subdomain (" + std::to_string((int64_t)h->max_nb * 32) +
                                             " padded columns) needs " + std::to_string(need) +
@@ -1391,6 +1421,12 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   if (h->opt.time_kernels)
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
   std::memset(h->pin, 0, sizeof(double) * lsq::S_NSLOT);
+  {
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+    h->r.zero(st);
+    choose_local_config(h, optin);
+  }
   block_plan(h);
   CK(cudaStreamSynchronize(st));
   h->sinfo.t_setup = now_s() - t_begin;
@@ -1398,6 +1434,7 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->sinfo.lanes_csr = h->lanes_csr;
   h->sinfo.lanes_csc = h->lanes_csc;
   h->sinfo.normal_product = h->normal_kind;
+  h->sinfo.local_config = h->local_cfg;
 }
 
 }  // namespace
@@ -1450,6 +1487,7 @@ void ls_default_options(ls_options* o) {
   o->block_kernel = 0;
   o->normal_product = 0;
   o->normal_kernel = 0;
+  o->local_config = 0;
 }
 
 const char* ls_last_error(void) { return g_err.c_str(); }
@@ -1483,6 +1521,7 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.block_kernel < 0 || h->opt.block_kernel > 2) throw LsError(LS_ERR_INVALID, "block_kernel must be 0, 1 or 2");
     if (h->opt.normal_product < 0 || h->opt.normal_product > 2)
       throw LsError(LS_ERR_INVALID, "normal_product must be 0, 1 or 2");
+    if (h->opt.local_config < 0 || h->opt.local_config > 2) throw LsError(LS_ERR_INVALID, "local_config must be 0, 1 or 2");
     if (h->opt.normal_kernel < 0 || h->opt.normal_kernel > 4)
       throw LsError(LS_ERR_INVALID, "normal_kernel must lie in [0, 4]");
     if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))

@@ -533,7 +533,7 @@ bool block_core(ls_handle* h, int R, double rtol, int mode, const std::vector<do
   inf.n0 = h->sinfo.n0; inf.kmin = h->sinfo.kmin; inf.kmax = h->sinfo.kmax; inf.tau_used = h->sinfo.tau_used;
   inf.delta = h->sinfo.delta; inf.t_setup = h->sinfo.t_setup; inf.t_eig = h->sinfo.t_eig;
   inf.eig_steps_max = h->sinfo.eig_steps_max;
-  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind;
+  inf.lanes_csr = h->lanes_csr; inf.lanes_csc = h->lanes_csc; inf.normal_product = h->normal_kind; inf.local_config = h->local_cfg;
   inf.local_kernel = h->blk.use_tc ? h->blk.kernel : 0;
   return converged || fixed > 0;
 }

@@ -194,6 +194,7 @@ struct ls_handle {
   DevBuf<float> L32, tsc;
   DevBuf<__nv_bfloat16> L16;
   int max_nb = 0;
+  int local_cfg = 1;  // configuration of the single-vector local solve (option local_config)
   int64_t total_local = 0, total_blocks = 0, fac_elems = 0;
 
   bool coarse = false;

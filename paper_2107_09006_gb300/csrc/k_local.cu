@@ -55,14 +55,19 @@ template <> struct Val<__nv_bfloat16> {
   static __device__ __forceinline__ float f(__nv_bfloat16 x) { return __bfloat162float(x); }
 };
 
-constexpr int kStageBytes = 16384;
+// Two configurations: 256 threads with 16 KB stages (two CTAs per SM: many subdomains)
+// and 512 threads with 32 KB stages (one CTA per SM: subdomains that each have an SM to
+// themselves, where one CTA's own issue rate bounds the solve; twice the warps to hide
+// the latency of its dependent steps and twice the columns per stage over which the
+// per-stage bookkeeping is spread).
+constexpr int kStageStd = 16384, kStageFat = 32768;
 constexpr long long kWaitCycles = 4000000000ll;  // about two seconds at GB300 clocks
 
 // Byte offset of the local vector v in shared memory: after the ring, the reduction
 // buffers and the barriers, rounded up to 16 bytes (vector reads of v).
-template <class TA, int S>
+template <class TA, int S, int NT, int SB>
 __host__ __device__ constexpr size_t v_offset() {
-  return ((size_t)S * kStageBytes + (kWarps * 32 + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) + 15) / 16 * 16;
+  return ((size_t)S * SB + (NT + 64) * sizeof(TA) + (S + 1) * sizeof(uint64_t) + 15) / 16 * 16;
 }
 
 // Order of the chunks one CTA consumes: forward sweep, blocks ascending, each segment's
@@ -91,27 +96,30 @@ struct ChunkIter {
   }
 };
 
-template <class TF, class TA, int S>
-__global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
+template <class TF, class TA, int S, int NT, int SB>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_local_solve(LocalArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NW = NT / 32;                   // warps
   constexpr int ES = sizeof(TF);
-  constexpr int CC = kStageBytes / (kT * ES);  // columns per stage
+  constexpr int CC = SB / (kT * ES);            // columns per stage
   constexpr int CHUNK = CC * kT;                // elements per stage
-  constexpr int G = kThreads / CC;              // row groups of the backward panel update
+  constexpr int G = NT / CC;                    // row groups of the backward panel update
   constexpr int RG = kT / G;                    // rows per group
   constexpr bool kSplit = (ES == 8);            // spread the 32x32 products over the warps
   constexpr bool kVec = (sizeof(TA) == 4);      // FP32 arithmetic: vectorised inner loops
-  constexpr int CPW = CC / kWarps;              // forward: contiguous columns per warp
+  constexpr int CPW = CC / NW;                  // forward: contiguous columns per warp
   constexpr int XG = 16 / ES;                   // rows per 16-byte read of a column
-  static_assert(G * CC == kThreads && G * RG == kT, "stage geometry");
-  static_assert(!kVec || (CPW % 4 == 0 && CC <= kThreads), "vectorised geometry");
+  constexpr int DC = kT / NW;                   // FP64 diagonal products: columns per warp
+  static_assert(G * CC == NT && G * RG == kT, "stage geometry");
+  static_assert(!kVec || (CPW % 4 == 0 && CC <= NT), "vectorised geometry");
+  static_assert(DC * NW == kT && (DC & (DC - 1)) == 0, "diagonal split");
   TF* ring = reinterpret_cast<TF*>(smem_raw);
-  TA* red = reinterpret_cast<TA*>(smem_raw + S * kStageBytes);
-  TA* tv = red + kWarps * 32;
+  TA* red = reinterpret_cast<TA*>(smem_raw + S * SB);
+  TA* tv = red + NW * 32;
   TA* xv = tv + 32;
   uint64_t* bars = reinterpret_cast<uint64_t*>(xv + 32);
   int* abort_flag = reinterpret_cast<int*>(bars + S);
-  TA* v = reinterpret_cast<TA*>(smem_raw + v_offset<TA, S>());  // 16-byte aligned
+  TA* v = reinterpret_cast<TA*>(smem_raw + v_offset<TA, S, NT, SB>());  // 16-byte aligned
 
   const int i = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
   // The copies are issued by the last warp: warp 0 carries the diagonal products of the
   // dependency chain, while the last warp's columns of a stage are most often the
   // diagonal tile's, which the panel products skip.
-  const bool issuer = tid == kThreads - 32;
+  const bool issuer = tid == NT - 32;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     *abort_flag = 0;
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
     const int64_t io = a.int_off[i];
     const int nIi = (int)(a.int_off[i + 1] - io);
     const double* Zi = a.Z + a.zoff[i];
-    for (int t = w; t < kk; t += kWarps) {
+    for (int t = w; t < kk; t += NW) {
       double acc = 0.0;
       for (int jj = lane; jj < nIi; jj += 32) acc += Zi[(int64_t)t * nIi + jj] * a.r[a.int_glob[io + jj]];
       acc = warp_sum(acc);
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
         if (w == 0) {
           TA s = 0;
 #pragma unroll
-          for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+          for (int u = 0; u < NW; ++u) s += red[u * 32 + lane];
           tv[lane] = v[b * kT + lane] - s;
           __syncwarp();
           if (!kSplit) {
@@ -288,13 +296,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           __syncthreads();
           TA x = 0;
 #pragma unroll
-          for (int c = 4 * w; c < 4 * w + 4; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
+          for (int c = DC * w; c < DC * w + DC; ++c) x += Val<TF>::f(D[c * kT + lane]) * tv[c];
           red[w * 32 + lane] = x;
           __syncthreads();
           if (w == 0) {
             TA s = 0;
 #pragma unroll
-            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+            for (int u = 0; u < NW; ++u) s += red[u * 32 + lane];
             v[b * kT + lane] = s * dsc;
           }
         }
@@ -322,8 +330,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           // (v_b is final: the last panel update reaching it ended with the previous stage)
           TA x = 0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = 4 * w + ((u + lane) & 3);
+          for (int u = 0; u < DC; ++u) {
+            const int r = DC * w + ((u + lane) & (DC - 1));
             x += Val<TF>::f(D[lane * kT + r]) * v[b * kT + r];
           }
           red[w * 32 + lane] = x;
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_local_solve(LocalArgs a) {
           if (w == 0) {
             TA s = 0;
 #pragma unroll
-            for (int u = 0; u < kWarps; ++u) s += red[u * 32 + lane];
+            for (int u = 0; u < NW; ++u) s += red[u * 32 + lane];
             s *= dsc;
             xv[lane] = s;
             v[b * kT + lane] = s;
@@ -481,36 +489,49 @@ __global__ void __launch_bounds__(kThreads) k_to_solve_layout<__nv_bfloat16>(con
   }
 }
 
-template <class TF, class TA, int S>
+template <class TF, class TA, int S, int NT, int SB>
 size_t smem_bytes(int max_nb) {
-  return v_offset<TA, S>() + (size_t)max_nb * (kT * sizeof(TA) + sizeof(int64_t) + sizeof(int32_t));
+  return v_offset<TA, S, NT, SB>() + (size_t)max_nb * (kT * sizeof(TA) + sizeof(int64_t) + sizeof(int32_t));
 }
 
-template <class TF, class TA, int S>
+template <class TF, class TA, int S, int NT, int SB>
 void launch_impl(int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
   static size_t raised = 0;
-  const size_t sm = smem_bytes<TF, TA, S>(max_nb);
+  const size_t sm = smem_bytes<TF, TA, S, NT, SB>(max_nb);
   if (sm > 48 * 1024 && sm > raised) {
-    cudaFuncSetAttribute(k_local_solve<TF, TA, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_local_solve<TF, TA, S, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     raised = sm;
   }
-  k_local_solve<TF, TA, S><<<N, kThreads, sm, st>>>(a);
+  k_local_solve<TF, TA, S, NT, SB><<<N, NT, sm, st>>>(a);
 }
 
 }  // namespace
 
-// Stages per precision: as deep a ring as two CTAs per SM allow (228 KB per SM) for
-// subdomains of up to 181 block rows.
-size_t local_solve_smem(int prec, int max_nb) {
-  if (prec == 0) return smem_bytes<double, double, 3>(max_nb);
-  if (prec == 1) return smem_bytes<float, float, 5>(max_nb);
-  return smem_bytes<__nv_bfloat16, float, 5>(max_nb);
+// Configuration 1 (256 threads, 16 KB stages): as deep a ring as two CTAs per SM allow
+// (228 KB per SM) for subdomains of up to 181 block rows.  Configuration 2 (512
+// threads, 32 KB stages, one CTA per SM): four stages (two for FP64, whose local vector
+// is twice as large).
+size_t local_solve_smem(int prec, int max_nb, int config) {
+  if (config == 2) {
+    if (prec == 0) return smem_bytes<double, double, 2, 512, kStageFat>(max_nb);
+    if (prec == 1) return smem_bytes<float, float, 4, 512, kStageFat>(max_nb);
+    return smem_bytes<__nv_bfloat16, float, 4, 512, kStageFat>(max_nb);
+  }
+  if (prec == 0) return smem_bytes<double, double, 3, 256, kStageStd>(max_nb);
+  if (prec == 1) return smem_bytes<float, float, 5, 256, kStageStd>(max_nb);
+  return smem_bytes<__nv_bfloat16, float, 5, 256, kStageStd>(max_nb);
 }
 
-void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
-  if (prec == 0) launch_impl<double, double, 3>(N, max_nb, a, st);
-  else if (prec == 1) launch_impl<float, float, 5>(N, max_nb, a, st);
-  else launch_impl<__nv_bfloat16, float, 5>(N, max_nb, a, st);
+void launch_local_solve(int prec, int config, int N, int max_nb, const LocalArgs& a, cudaStream_t st) {
+  if (config == 2) {
+    if (prec == 0) launch_impl<double, double, 2, 512, kStageFat>(N, max_nb, a, st);
+    else if (prec == 1) launch_impl<float, float, 4, 512, kStageFat>(N, max_nb, a, st);
+    else launch_impl<__nv_bfloat16, float, 4, 512, kStageFat>(N, max_nb, a, st);
+    return;
+  }
+  if (prec == 0) launch_impl<double, double, 3, 256, kStageStd>(N, max_nb, a, st);
+  else if (prec == 1) launch_impl<float, float, 5, 256, kStageStd>(N, max_nb, a, st);
+  else launch_impl<__nv_bfloat16, float, 5, 256, kStageStd>(N, max_nb, a, st);
 }
 
 void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,

@@ -171,8 +171,10 @@ struct LocalArgs {
   int stall;    // test hook: 1 issues no copies, so the bounded waits run out
   int64_t n_cols, fac_elems;  // bounds of the gather indices and the factor (bounds-checked build)
 };
-size_t local_solve_smem(int prec, int max_nb);
-void launch_local_solve(int prec, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
+// config 1: 256 threads, 16 KB stages (two CTAs per SM); 2: 512 threads, 32 KB stages
+// (one CTA per SM).
+size_t local_solve_smem(int prec, int max_nb, int config);
+void launch_local_solve(int prec, int config, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
 // Block-envelope factor + inverse diagonal tiles (FP64) -> solve storage (prec 0/1/2);
 // tsc receives one scale per 32x32 tile for BF16.
 void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,

@@ -60,9 +60,10 @@ def test_eigenvalues_and_coarse_dimension(big):
     S.close()
 
 
+@pytest.mark.parametrize("config", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-5)])
-def test_two_level_apply(big, prec, tol):
-    S = _solver(big, factor_prec=prec)
+def test_two_level_apply(big, prec, tol, config):
+    S = _solver(big, factor_prec=prec, local_config=config)
     r = np.random.default_rng(3).standard_normal(big["n"])
     assert rel(S.apply_preconditioner(r, 0).cpu().numpy(), big["M"].apply(r)) < tol
     S.close()

@@ -93,19 +93,21 @@ def test_coarse_dimension_and_two_level_apply_fp64(geo):
     S.close()
 
 
-def test_pcg_fixed_iterations_fp64(geo):
+@pytest.mark.parametrize("config", [1, 2])
+def test_pcg_fixed_iterations_fp64(geo, config):
     P, M = geo["P"], geo["M"]
-    S = _solver(geo, fixed_iters=6)
+    S = _solver(geo, fixed_iters=6, local_config=config)
     x, _ = S.solve(P.b, rtol=1e-8)
     xo, _ = O.pcg(geo["A"], P.b, M.apply, fixed_iters=6)
     assert rel(x.cpu().numpy(), xo) < 1e-10
     S.close()
 
 
+@pytest.mark.parametrize("config", [1, 2])
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_one_level_apply_mixed(geo, prec):
+def test_one_level_apply_mixed(geo, prec, config):
     M = geo["M"]
-    S = _solver(geo, coarse=0, factor_prec=prec)
+    S = _solver(geo, coarse=0, factor_prec=prec, local_config=config)
     r = np.random.default_rng(4).standard_normal(geo["P"].n)
     exact = M.apply_local(r)
     e_dev = rel(S.apply_preconditioner(r, 1).cpu().numpy(), exact)

@@ -95,8 +95,12 @@ def test_normal_product(case):
     S.close()
 
 
-def test_one_level_apply(case):
-    S = case.solver(coarse=0)
+@pytest.mark.parametrize("config", [1, 2])
+def test_one_level_apply(case, config):
+    """Both configurations of the local solve (option local_config: 256 threads with 16 KB
+    stages, 512 threads with 32 KB stages)."""
+    S = case.solver(coarse=0, local_config=config)
+    assert S.info()["local_config"] == config
     M = case.oracle(coarse=False)
     r = np.random.default_rng(2).standard_normal(case.n)
     assert rel(S.apply_preconditioner(r, 1).cpu().numpy(), M.apply_local(r)) < 1e-12
@@ -146,8 +150,9 @@ def test_coarse_span_matches(case):
     S.close()
 
 
-def test_pcg_fixed_iterations(case):
-    S = case.solver(fixed_iters=6)
+@pytest.mark.parametrize("config", [1, 2])
+def test_pcg_fixed_iterations(case, config):
+    S = case.solver(fixed_iters=6, local_config=config)
     M = case.oracle()
     x, _ = S.solve(case.b, rtol=1e-8)
     xo, _ = O.pcg(case.A, case.b, M.apply, fixed_iters=6)

@@ -25,9 +25,12 @@ import oracle as O  # noqa: E402
 from workloads import config_tiny  # noqa: E402
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("prec,config", [("f64", 1), ("f64", 2), ("f32", 2)])
+def test_bounded_wait_reports_timeout_and_context_survives(prec, config):
+    """Both local-solve configurations (option local_config) take the error path."""
     P = config_tiny()
-    S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, test_stall=1)
+    S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, test_stall=1, factor_prec=prec,
+                 local_config=config)
     t0 = time.time()
     with pytest.raises(L.LSError) as ex:
         S.solve(P.b, rtol=1e-8)
