@@ -46,18 +46,28 @@ __device__ void band_forward(const TF* __restrict__ fac, const float* __restrict
     const int64_t po = B.poff[b];
     const TF* pan = fac + po;
     const TA* vw = v + t0 * kT;
-    for (int rr = w * 4; rr < w * 4 + 4; ++rr) {
-      const TF* row = pan + (int64_t)rr * width;
-      TA acc = 0;
-      if (tsc) {
-        int tcol = 0;
-        for (int c = lane; c < offw; c += 32, ++tcol)
-          acc += (TA)tsc[po / 1024 + tcol] * (Load<TF>::get(row, c) * vw[c]);
-      } else {
-        for (int c = lane; c < offw; c += 32) acc += Load<TF>::get(row, c) * vw[c];
+    // the warp's four rows in one pass (four independent loads per column step; each
+    // row's sum keeps its order)
+    const TF* row0 = pan + (int64_t)(w * 4) * width;
+    TA acc[4] = {0, 0, 0, 0};
+    if (tsc) {
+      int tcol = 0;
+      for (int c = lane; c < offw; c += 32, ++tcol) {
+        const TA x = vw[c], sc = (TA)tsc[po / 1024 + tcol];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += sc * (Load<TF>::get(row0 + (int64_t)q * width, c) * x);
       }
-      acc = warp_sum(acc);
-      if (lane == 0) tmp[rr] = v[b * kT + rr] - acc;
+    } else {
+      for (int c = lane; c < offw; c += 32) {
+        const TA x = vw[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += Load<TF>::get(row0 + (int64_t)q * width, c) * x;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const TA sum = warp_sum(acc[q]);
+      if (lane == 0) tmp[w * 4 + q] = v[b * kT + w * 4 + q] - sum;
     }
     const TA dsc = tsc ? (TA)tsc[po / 1024 + (b - t0)] : (TA)1;
     for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
@@ -129,18 +139,29 @@ __device__ void band_symv(const double* __restrict__ fac, BandRef B, const TA* x
     const int offw = width - kT;
     const double* pan = fac + B.poff[b];
     const TA* xw = x + t0 * kT;
-    for (int rr = w * 4; rr < w * 4 + 4; ++rr) {
-      const double* row = pan + (int64_t)rr * width;
-      TA acc = 0;
-      for (int c = lane; c <= offw + rr; c += 32) acc += row[c] * xw[c];
-      acc = warp_sum(acc);
-      if (lane == 0) y[b * kT + rr] += acc;
+    // the warp's four rows in one pass (row rr sums columns c <= offw + rr, in order)
+    const double* row0 = pan + (int64_t)(w * 4) * width;
+    TA acc[4] = {0, 0, 0, 0};
+    for (int c = lane; c <= offw + w * 4 + 3; c += 32) {
+      const TA xc = xw[c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c <= offw + w * 4 + q) acc[q] += row0[(int64_t)q * width + c] * xc;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const TA sum = warp_sum(acc[q]);
+      if (lane == 0) y[b * kT + w * 4 + q] += sum;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < width; c += blockDim.x) {
       TA acc = 0;
-      const int rs = (c < offw) ? 0 : (c - offw + 1);
-      for (int rr = rs; rr < kT; ++rr) acc += pan[(int64_t)rr * width + c] * x[b * kT + rr];
+      if (c < offw) {
+#pragma unroll 8
+        for (int rr = 0; rr < kT; ++rr) acc += pan[(int64_t)rr * width + c] * x[b * kT + rr];
+      } else {
+        for (int rr = c - offw + 1; rr < kT; ++rr) acc += pan[(int64_t)rr * width + c] * x[b * kT + rr];
+      }
       y[t0 * kT + c] += acc;
     }
     __syncthreads();

@@ -61,15 +61,27 @@ __device__ void apply_T(const EigArgs& a, BandRef B, const uint8_t* isint, int n
                                s.x2, s.dt, s.tmp);
 }
 
-// h[t] = V_t . x for t < nv (one warp per t).
+// h[t] = V_t . x for t < nv (one warp per t, two vectors per warp at a time for more
+// loads in flight; each sum keeps its order).
 __device__ void project(const double* V, int64_t vs, int nv, const double* x, int npad, double* h) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int t = w; t < nv; t += kWarps) {
+  for (int t = w; t < nv; t += 2 * kWarps) {
+    const int t2 = t + kWarps;
     const double* vt = V + t * vs;
-    double acc = 0.0;
-    for (int k = lane; k < npad; k += 32) acc += vt[k] * x[k];
+    const double* vu = V + (int64_t)min(t2, nv - 1) * vs;
+    double acc = 0.0, acc2 = 0.0;
+#pragma unroll 4
+    for (int k = lane; k < npad; k += 32) {
+      const double xk = x[k];
+      acc += vt[k] * xk;
+      acc2 += vu[k] * xk;
+    }
     acc = warp_sum(acc);
-    if (lane == 0) h[t] = acc;
+    acc2 = warp_sum(acc2);
+    if (lane == 0) {
+      h[t] = acc;
+      if (t2 < nv) h[t2] = acc2;
+    }
   }
   __syncthreads();
 }
@@ -78,6 +90,7 @@ __device__ void project(const double* V, int64_t vs, int nv, const double* x, in
 __device__ void subtract(const double* V, int64_t vs, int nv, const double* h, double* x, int npad) {
   for (int k = threadIdx.x; k < npad; k += blockDim.x) {
     double acc = 0.0;
+#pragma unroll 8
     for (int t = 0; t < nv; ++t) acc += V[t * vs + k] * h[t];
     x[k] -= acc;
   }
