@@ -132,9 +132,14 @@ typedef struct {
     int local_config;  /* single-vector local solve: 1 blocks of 256 threads with 16 KB
                           stages, two per SM (many subdomains); 2 blocks of 512 threads
                           with 32 KB stages, one per SM (subdomains that each get an SM:
-                          twice the warps, twice the columns per stage); 0 (the default)
-                          times both at the end of setup when both fit the shared
-                          memory and keeps the faster.  ls_info.local_config reports it. */
+                          twice the warps, twice the columns per stage); 3 (FP32 factors)
+                          each subdomain split over a cluster of 2 such blocks on two
+                          SMs, which share its factor stream and exchange partial sums
+                          and solution blocks through distributed shared memory (when
+                          twice the subdomain count does not exceed the SM count); 0 (the
+                          default) times those that fit at the end of setup and keeps
+                          the fastest (LS_ERR_UNSUPPORTED when a forced one does not
+                          fit).  ls_info.local_config reports it.                      */
 } ls_options;
 
 typedef struct {

@@ -115,37 +115,59 @@ void launch_local(ls_handle* h, const double* rin, bool with_coarse) {
   a.Z = h->Z.p; a.r0 = h->r0.p;
   a.stall = h->opt.test_stall;
   a.n_cols = h->n; a.fac_elems = h->fac_elems;
+  if (h->local_cfg == 3) {
+    if (!lsq::local_split_launch(h->N, h->max_nb, a, h->st))
+      throw LsError(LS_ERR_CUDA, std::string("local solve (cluster launch): ") + cudaGetErrorString(cudaGetLastError()));
+    return;
+  }
   lsq::launch_local_solve(h->prec, h->local_cfg, h->N, h->max_nb, a, h->st);
 }
 
-// The local-solve configuration: forced by the option, else both timed on the factors
-// (two launches each after a warm one) when both fit the shared memory.
+// The local-solve configuration: forced by the option, else the candidates that fit
+// timed on the factors (two launches each after a warm one).  Configuration 3 (FP32
+// factors only) splits each subdomain over a cluster of CTAs; it is a candidate when
+// every CTA of every cluster can have an SM of its own.
 void choose_local_config(ls_handle* h, int optin) {
   h->local_cfg = 1;
-  const bool fat_fits = lsq::local_solve_smem(h->prec, h->max_nb, 2) <= (size_t)optin;
-  if (h->opt.local_config == 2) {
-    if (!fat_fits) throw LsError(LS_ERR_UNSUPPORTED, "local_config = 2: the largest subdomain does not fit");
-    h->local_cfg = 2;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev));
+  const bool fits[4] = {false, true, lsq::local_solve_smem(h->prec, h->max_nb, 2) <= (size_t)optin,
+                        h->prec == LS_PREC_F32 && lsq::local_split_smem(h->max_nb) <= (size_t)optin &&
+                            (int64_t)h->N * lsq::local_split_cluster() <= sms};
+  if (h->opt.local_config != 0) {
+    if (!fits[h->opt.local_config])
+      throw LsError(LS_ERR_UNSUPPORTED, "local_config = " + std::to_string(h->opt.local_config) +
+                                            ": not available for this factor precision, subdomain count or size");
+    h->local_cfg = h->opt.local_config;
     return;
   }
-  if (h->opt.local_config == 1 || !fat_fits || h->opt.test_stall) return;
+  if (h->opt.test_stall) return;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float ms[3] = {0.f, 0.f, 0.f};
-  for (int cfg = 1; cfg <= 2; ++cfg) {
+  float best = 1e30f;
+  int pick = 1;
+  for (int cfg = 1; cfg <= 3; ++cfg) {
+    if (!fits[cfg]) continue;
     h->local_cfg = cfg;
-    launch_local(h, h->r.p, false);
+    try {
+      launch_local(h, h->r.p, false);
+    } catch (const LsError&) {
+      cudaGetLastError();  // a refused cluster launch: the configuration is not a candidate
+      continue;
+    }
     CK(cudaEventRecord(e0, h->st));
     for (int k = 0; k < 2; ++k) launch_local(h, h->r.p, false);
     CK(cudaEventRecord(e1, h->st));
     CK(cudaEventSynchronize(e1));
-    CK(cudaEventElapsedTime(&ms[cfg], e0, e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; pick = cfg; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   check_launch("local-solve configuration timing");
-  h->local_cfg = ms[2] < ms[1] ? 2 : 1;
+  h->local_cfg = pick;
 }
 
 // out = Q v = R_0^T C_00^{-1} R_0 v (restriction, dense coarse solve, prolongation)
@@ -1521,7 +1543,7 @@ ls_status setup_entry(int32_t nprob, const int64_t* m_off, const int64_t* n_off,
     if (h->opt.block_kernel < 0 || h->opt.block_kernel > 2) throw LsError(LS_ERR_INVALID, "block_kernel must be 0, 1 or 2");
     if (h->opt.normal_product < 0 || h->opt.normal_product > 2)
       throw LsError(LS_ERR_INVALID, "normal_product must be 0, 1 or 2");
-    if (h->opt.local_config < 0 || h->opt.local_config > 2) throw LsError(LS_ERR_INVALID, "local_config must be 0, 1 or 2");
+    if (h->opt.local_config < 0 || h->opt.local_config > 3) throw LsError(LS_ERR_INVALID, "local_config must lie in [0, 3]");
     if (h->opt.normal_kernel < 0 || h->opt.normal_kernel > 4)
       throw LsError(LS_ERR_INVALID, "normal_kernel must lie in [0, 4]");
     if (h->opt.spmv != 0 && !lsq::valid_spmv_code(h->opt.spmv))
@@ -1681,6 +1703,7 @@ ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int 
     if (!h || !r || !z || which < 0 || which > 2) throw LsError(LS_ERR_INVALID, "bad arguments");
     if (h->nprob > 1) throw LsError(LS_ERR_UNSUPPORTED, "single-vector preconditioner apply on a batched handle");
     CK(cudaSetDevice(h->dev));
+    CK(cudaMemsetAsync(h->scal.p + lsq::S_ERR, 0, sizeof(double), h->st));
     CK(cudaMemcpyAsync(h->tv.p, r, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     if (which == 2) {
       // the coarse term Q r alone
@@ -1692,6 +1715,11 @@ ls_status ls_apply_preconditioner(ls_handle* h, const double* r, double* z, int 
     CK(cudaMemcpyAsync(z, h->w.p, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
     CK(cudaStreamSynchronize(h->st));
     check_launch("preconditioner");
+    double err = 0.0;
+    CK(cudaMemcpy(&err, h->scal.p + lsq::S_ERR, sizeof(double), cudaMemcpyDeviceToHost));
+    if (err == lsq::kErrBounds)
+      throw LsError(LS_ERR_INVALID, "an index out of range was met (bounds-checked build) in the preconditioner apply");
+    if (err != 0.0) throw LsError(LS_ERR_DEVICE_TIMEOUT, "a bounded wait in the local-solve kernel gave up");
     return LS_OK;
   });
 }

@@ -175,6 +175,12 @@ struct LocalArgs {
 // (one CTA per SM).
 size_t local_solve_smem(int prec, int max_nb, int config);
 void launch_local_solve(int prec, int config, int N, int max_nb, const LocalArgs& a, cudaStream_t st);
+// Configuration 3 (FP32 factors, k_local_split.cu): each subdomain split over a cluster of
+// local_split_cluster() CTAs of 512 threads.  The launcher returns false if the launch
+// was refused (the caller keeps another configuration).
+size_t local_split_smem(int max_nb);
+int local_split_cluster();
+bool local_split_launch(int N, int max_nb, const LocalArgs& a, cudaStream_t st);
 // Block-envelope factor + inverse diagonal tiles (FP64) -> solve storage (prec 0/1/2);
 // tsc receives one scale per 32x32 tile for BF16.
 void launch_to_solve_layout(int prec, int64_t nblocks, const int64_t* poff, const double* L, const double* dinv,

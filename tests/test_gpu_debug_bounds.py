@@ -5,7 +5,7 @@ factor copy range in the local-solve, scatter and block local-solve kernels; an 
 of range would be reported as LS_ERR_INVALID instead of being used.  On valid inputs the
 checks must change nothing: a child process that loads the checked build
 (LS_SCHWARZ_BOUNDS=1) solves the same problems as this process with the product build,
-through the single-vector path (FP64 and FP32 factors, and the row-tile normal product)
+through the single-vector path (FP64 and FP32 factors, the cluster-split FP32 local solve, and the row-tile normal product)
 and both tensor-core kernels of the block path, and the iterates agree: to 1e-12 in FP64 and 1e-6 with FP32 factors (the
 checks add no arithmetic, but the compiler may contract or order the FP32 sums of the
 checked build differently).  A check that fired on a valid index would fail the child's
@@ -43,6 +43,10 @@ for prec in ("f64", "f32"):
                  fixed_iters=6)
     out["tiny-" + prec] = S.solve(P.b, rtol=1e-8)[0].cpu().numpy().tolist()
     S.close()
+S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, factor_prec="f32", spmv=2,
+             local_config=3, fixed_iters=6)
+out["tiny-split-f32"] = S.solve(P.b, rtol=1e-8)[0].cpu().numpy().tolist()
+S.close()
 S = L.Solver(m, n, rp, c, v, part, 9, nev_max=16, normal_product=2, normal_kernel=4, fixed_iters=6)
 out["tiles-f64"] = S.solve(b[0], rtol=1e-8)[0].cpu().numpy().tolist()
 S.close()

@@ -60,8 +60,8 @@ def test_eigenvalues_and_coarse_dimension(big):
     S.close()
 
 
-@pytest.mark.parametrize("config", [1, 2])
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-5)])
+@pytest.mark.parametrize("prec,tol,config", [("f64", 1e-9, 1), ("f64", 1e-9, 2), ("f32", 1e-5, 1), ("f32", 1e-5, 2),
+                                             ("f32", 1e-5, 3)])
 def test_two_level_apply(big, prec, tol, config):
     S = _solver(big, factor_prec=prec, local_config=config)
     r = np.random.default_rng(3).standard_normal(big["n"])

@@ -103,8 +103,7 @@ def test_pcg_fixed_iterations_fp64(geo, config):
     S.close()
 
 
-@pytest.mark.parametrize("config", [1, 2])
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("prec,config", [("f32", 1), ("f32", 2), ("f32", 3), ("bf16", 1), ("bf16", 2)])
 def test_one_level_apply_mixed(geo, prec, config):
     M = geo["M"]
     S = _solver(geo, coarse=0, factor_prec=prec, local_config=config)

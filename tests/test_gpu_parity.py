@@ -150,6 +150,30 @@ def test_coarse_span_matches(case):
     S.close()
 
 
+def test_split_local_solve(case):
+    """Local-solve configuration 3 (FP32 factors; each subdomain split over a cluster of
+    two CTAs that exchange partial sums and solution blocks through distributed shared
+    memory; the paper example and the tiny case have subdomains of one or two block
+    rows, in which the second CTA owns no chunk): the one-level apply against the oracle
+    within the FP32 tolerance of the other configurations, against configuration 1 to
+    FP32 rounding, and a converged solve."""
+    M = case.oracle(coarse=False)
+    r = np.random.default_rng(2).standard_normal(case.n)
+    S = case.solver(coarse=0, factor_prec="f32", local_config=3)
+    assert S.info()["local_config"] == 3
+    z3 = S.apply_preconditioner(r, 1).cpu().numpy()
+    S.close()
+    S = case.solver(coarse=0, factor_prec="f32", local_config=1)
+    z1 = S.apply_preconditioner(r, 1).cpu().numpy()
+    S.close()
+    exact = M.apply_local(r)
+    assert rel(z3, exact) < 1e-5 and rel(z3, z1) < 1e-5
+    S = case.solver(factor_prec="f32", local_config=3)
+    x, info = S.solve(case.b, rtol=1e-8)
+    assert info["relres_true"] <= 1e-8
+    S.close()
+
+
 @pytest.mark.parametrize("config", [1, 2])
 def test_pcg_fixed_iterations(case, config):
     S = case.solver(fixed_iters=6, local_config=config)

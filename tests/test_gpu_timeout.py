@@ -25,9 +25,11 @@ import oracle as O  # noqa: E402
 from workloads import config_tiny  # noqa: E402
 
 
-@pytest.mark.parametrize("prec,config", [("f64", 1), ("f64", 2), ("f32", 2)])
+@pytest.mark.parametrize("prec,config", [("f64", 1), ("f64", 2), ("f32", 2), ("f32", 3)])
 def test_bounded_wait_reports_timeout_and_context_survives(prec, config):
-    """Both local-solve configurations (option local_config) take the error path."""
+    """Every local-solve configuration (option local_config) takes the error path; in
+    the split configuration both CTAs of a cluster give up and meet at the cluster
+    barrier before leaving."""
     P = config_tiny()
     S = L.Solver(P.m, P.n, P.row_ptr, P.col, P.val, P.part, P.nparts, nev_max=16, test_stall=1, factor_prec=prec,
                  local_config=config)
