@@ -276,20 +276,17 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_local_split(LocalArgs a) {
       // before the row: the values this CTA reads (v up to block b - rank T in the
       // forward sweep, x_b in the backward sweep); waiting at every row also keeps the
       // senders within the message ring
+      // Every thread polls the message barrier itself (its own acquire), so no CTA
+      // barrier follows; a wait that gives up is acted on at the next uniform check.
       if (rank > 0) {
         const int j = sweep == 0 ? b - rank * T : nb - 1 - b;  // message place in the sweep
-        if (j >= 0) {
-          if (w == 0) {
-            bounded_wait<true>(sweep == 0 ? &vf[j % D] : &xf[j % D], (uint32_t)((j / D) & 1), abort_flag);
-            if (sweep == 1 && has) xv[lane] = xbuf[(j % D) * 32 + lane];
-          }
-          __syncthreads();
-          if (*abort_flag) break;
-        }
+        if (j >= 0)
+          bounded_wait<true>(sweep == 0 ? &vf[j % D] : &xf[j % D], (uint32_t)((j / D) & 1), abort_flag);
         if (sweep == 1 && has) {
+          const float* xb = xbuf + (j % D) * 32;
 #pragma unroll
           for (int g = 0; g < kT / 4; ++g) {
-            const float4 t4 = *reinterpret_cast<const float4*>(xv + ((g + rot) & (kT / 4 - 1)) * 4);
+            const float4 t4 = *reinterpret_cast<const float4*>(xb + ((g + rot) & (kT / 4 - 1)) * 4);
             xr[4 * g] = t4.x; xr[4 * g + 1] = t4.y; xr[4 * g + 2] = t4.z; xr[4 * g + 3] = t4.w;
           }
         }
@@ -438,9 +435,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_local_split(LocalArgs a) {
             arrive_peer(peer_addr(&df[o % D], 0));
           }
         }
-        __syncthreads();  // red and v are read by warp 0 above before any warp writes them again
+        // (no barrier here: red is written again only after a later chunk's barrier, which
+        // warp 0 reaches after reading it, and this CTA never updates block b - rank T
+        // again after row b)
       }
     }
+    __syncthreads();  // a uniform view of the abort flag before the next sweep or the exit
   }
   if (*abort_flag) {
     if (issuer) {
