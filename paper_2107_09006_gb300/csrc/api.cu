@@ -141,7 +141,7 @@ void choose_local_config(ls_handle* h, int optin) {
     h->local_cfg = h->opt.local_config;
     return;
   }
-  if (h->opt.test_stall) return;
+  if (h->opt.test_stall || h->nprob > 1) return;  // (batched handles solve through the block path)
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1067,8 +1067,9 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     h->sellB_col.upload(sb.col, st); h->sellB_val.upload(sb.val, st);
     CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
   }
-  // row tiles of the one-pass normal product (a candidate unless a kernel is forced)
-  if (h->opt.normal_product == 2 || (h->opt.normal_product == 0 && h->opt.spmv == 0)) {
+  // row tiles of the one-pass normal product (a candidate unless a kernel is forced; not
+  // on batched handles, whose solves run the multi right-hand-side products)
+  if (h->opt.normal_product == 2 || (h->opt.normal_product == 0 && h->opt.spmv == 0 && h->nprob == 1)) {
     int smem_optin = 0;
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
     lsq::NormalTilesHost nt;
