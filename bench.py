@@ -32,10 +32,10 @@ METRIC = "n=1M LS solve s to 1e-8 normal-eq rel resid, mixed vs FP64 form; apply
 # DRAM bytes (read + write) of one k_local_solve launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one pass) on the workload,
 # form and local-solve configuration named in the key; valid while that kernel and
-# workload stay as they are (the capture: profiles/k_local_solve_dram_grid1024-N256_f32.md).
+# workload stay as they are (the capture's command and figures are kept with the profile summaries).
 LOCAL_SOLVE_TRAFFIC = {("grid1024-r3k8-N256", "f32", 1): 5.81e9 + 8.75e6}
 TRAFFIC_SOURCE = ("constant in bench.py from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of "
-                  "this kernel, workload, form and configuration: profiles/k_local_solve_dram_grid1024-N256_f32.md")
+                  "this kernel, workload, form and configuration (kept with the profile summaries of k_local_solve)")
 FALLBACK_HBM_GBS = 6800.0
 
 
