@@ -10,6 +10,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ls_schwarz.h"
@@ -867,6 +868,33 @@ std::vector<T> to_host(const T* src, size_t count) {
   return v;
 }
 
+// f(begin, end) over [0, count) split across the host's threads.
+template <class F>
+void host_parallel(int64_t count, F&& f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 4, 32));
+  if (count < 65536 || nt == 1) {
+    f((int64_t)0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t per = (count + nt - 1) / nt;
+  for (int64_t k = 0; k < nt; ++k) {
+    const int64_t a = k * per, b = std::min(count, a + per);
+    if (a < b) th.emplace_back([&f, a, b]() { f(a, b); });
+  }
+  for (auto& t : th) t.join();
+}
+
+// A host thread that is joined when the owner leaves its scope (also by an exception).
+struct HostJob {
+  std::thread t;
+  void join() {
+    if (t.joinable()) t.join();
+  }
+  ~HostJob() { join(); }
+};
+
 // The CSC and sliced-ELL copies of A' take their values from the CSR values h->val.
 void refresh_value_copies(ls_handle* h) {
   cudaStream_t st = h->st;
@@ -1000,16 +1028,18 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
     std::vector<int64_t> rp2(h->m + 1, 0), emap(nnz);
     std::vector<int32_t> c2(nnz);
     std::vector<double> v2(nnz);
-    for (int64_t r2 = 0; r2 < h->m; ++r2) {
-      const int32_t r = perm[r2];
-      const int64_t len = hrp[r + 1] - hrp[r];
-      rp2[r2 + 1] = rp2[r2] + len;
-      for (int64_t k = 0; k < len; ++k) {
-        c2[rp2[r2] + k] = hcol[hrp[r] + k];
-        v2[rp2[r2] + k] = hval[hrp[r] + k];
-        emap[rp2[r2] + k] = hrp[r] + k;
+    for (int64_t r2 = 0; r2 < h->m; ++r2) rp2[r2 + 1] = rp2[r2] + (hrp[perm[r2] + 1] - hrp[perm[r2]]);
+    host_parallel(h->m, [&](int64_t a, int64_t b) {
+      for (int64_t r2 = a; r2 < b; ++r2) {
+        const int32_t r = perm[r2];
+        const int64_t len = hrp[r + 1] - hrp[r];
+        for (int64_t k = 0; k < len; ++k) {
+          c2[rp2[r2] + k] = hcol[hrp[r] + k];
+          v2[rp2[r2] + k] = hval[hrp[r] + k];
+          emap[rp2[r2] + k] = hrp[r] + k;
+        }
       }
-    }
+    });
     h->perm.upload(perm, st);
     h->entmap.upload(emap, st);
     CK(cudaStreamSynchronize(st));
@@ -1039,62 +1069,50 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   h->lanes_csc = pow2_lanes((double)nnz / (double)h->n);
 
   // matrix copies
-  phase.next("ls_setup: matrix copies and sparse-product autotuning");
+  phase.next("ls_setup: matrix copies");
   h->row_ptr.upload(hrp, st);
   h->col.upload(hcol, st);
   h->val.upload(hval, st);
   h->col_ptr.upload(hs.csc_ptr, st);
   h->crow.upload(hs.csc_row, st);
-  {
-    std::vector<double> cv(nnz);
-    for (int64_t s = 0; s < nnz; ++s) cv[s] = hval[hs.csc_perm[s]];
-    h->cval.upload(cv, st);
-    // sliced-ELL copies of A and A^T (candidates of the product autotuner)
-    lsq::SellHost sa, sb;
-    lsq::build_sell(h->m, hrp.data(), hcol.data(), hval.data(), 256, sa);
-    lsq::build_sell(h->n, hs.csc_ptr.data(), hs.csc_row.data(), cv.data(), 256, sb);
-    // where every stored copy of an entry comes from (A' CSR slot), for ls_update_values
-    for (auto& e : sb.src)
-      if (e >= 0) e = hs.csc_perm[e];
-    h->cperm.upload(hs.csc_perm, st);
-    h->sellA_src.upload(sa.src, st);
-    h->sellB_src.upload(sb.src, st);
-    h->sellA.nslices = sa.nslices;
-    h->sellA_off.upload(sa.off, st); h->sellA_perm.upload(sa.perm, st);
-    h->sellA_col.upload(sa.col, st); h->sellA_val.upload(sa.val, st);
-    h->sellB.nslices = sb.nslices;
-    h->sellB_off.upload(sb.off, st); h->sellB_perm.upload(sb.perm, st);
-    h->sellB_col.upload(sb.col, st); h->sellB_val.upload(sb.val, st);
-    CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
-  }
-  // row tiles of the one-pass normal product (a candidate unless a kernel is forced; not
-  // on batched handles, whose solves run the multi right-hand-side products)
-  if (h->opt.normal_product == 2 || (h->opt.normal_product == 0 && h->opt.spmv == 0 && h->nprob == 1)) {
-    int smem_optin = 0;
-    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-    lsq::NormalTilesHost nt;
-    if (lsq::build_normal_tiles(h->m, h->n, hrp.data(), hcol.data(), hval.data(), smem_optin / 8 - 128, sms, nt)) {
-      h->nt_lo.upload(nt.lo, st); h->nt_wid.upload(nt.wid, st);
-      h->nt_as0.upload(nt.as0, st); h->nt_bs0.upload(nt.bs0, st);
-      h->nt_aoff.upload(nt.aoff, st); h->nt_acol.upload(nt.acol, st); h->nt_aval.upload(nt.aval, st);
-      h->nt_boff.upload(nt.boff, st); h->nt_brow.upload(nt.brow, st); h->nt_bval.upload(nt.bval, st);
-      h->nt_bcid.upload(nt.bcid, st); h->nt_poff.upload(nt.poff, st);
-      h->nt_asrc.upload(nt.asrc, st); h->nt_bsrc.upload(nt.bsrc, st);
-      h->nt_cb0.upload(nt.cb_t0, st); h->nt_cb1.upload(nt.cb_t1, st);
-      h->nt_part.alloc((size_t)nt.poff[nt.ntiles]);
-      h->nt_tiles = nt.ntiles;
-      h->nt_smem = nt.smem_doubles;
-      const int64_t st6[6] = {nt.ntiles, (int64_t)nt.aval.size(), (int64_t)nt.bval.size(), nt.as0[nt.ntiles],
-                              nt.bs0[nt.ntiles], nt.poff[nt.ntiles]};
-      for (int k = 0; k < 6; ++k) h->nt_stats[k] = st6[k];
-      CK(cudaStreamSynchronize(st));
-      if (!lsq::normal_tiles_prepare(ntiles(h))) release_normal_tiles(h);
-    }
-    if (h->nt_tiles == 0 && h->opt.normal_product == 2)
-      throw LsError(LS_ERR_UNSUPPORTED, "normal_product = 2: a row's column span does not fit a block's shared memory");
-  }
+  std::vector<double> cv(nnz);
+  host_parallel(nnz, [&](int64_t a, int64_t b) {
+    for (int64_t t = a; t < b; ++t) cv[t] = hval[hs.csc_perm[t]];
+  });
+  h->cval.upload(cv, st);
+  h->cperm.upload(hs.csc_perm, st);
   h->part.upload(hpart, st);
-  autotune_spmv(h);
+  // The copies that only the sparse-product autotuner needs (sliced ELL of A and A^T,
+  // the row tiles of the one-pass normal product: not on batched handles, whose solves
+  // run the multi right-hand-side products) are built by a host thread while the device
+  // runs the factorisations and eigensolves; the autotuning runs at the end of setup.
+  const bool want_tiles =
+      h->opt.normal_product == 2 || (h->opt.normal_product == 0 && h->opt.spmv == 0 && h->nprob == 1);
+  int smem_optin = 0;
+  CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  const int tile_cap = smem_optin / 8 - 128;
+  if (h->opt.normal_product == 2) {
+    // one row alone must fit a tile (its padded row and its column span)
+    for (int64_t r = 0; r < h->m; ++r)
+      if (hrp[r + 1] > hrp[r] && 32 + ((hcol[hrp[r + 1] - 1] - hcol[hrp[r]] + 2) & ~1) > tile_cap)
+        throw LsError(LS_ERR_UNSUPPORTED, "normal_product = 2: a row's column span does not fit a block's shared memory");
+  }
+  lsq::SellHost sa, sb;
+  lsq::NormalTilesHost nt;
+  bool nt_ok = false, job_failed = false;
+  HostJob job;  // declared after everything it reads: joined first on every way out
+  job.t = std::thread([&]() {
+    try {
+      lsq::build_sell(h->m, hrp.data(), hcol.data(), hval.data(), 256, sa);
+      lsq::build_sell(h->n, hs.csc_ptr.data(), hs.csc_row.data(), cv.data(), 256, sb);
+      // where every stored copy of an entry comes from (A' CSR slot), for ls_update_values
+      for (auto& e : sb.src)
+        if (e >= 0) e = hs.csc_perm[e];
+      if (want_tiles) nt_ok = lsq::build_normal_tiles(h->m, h->n, hrp.data(), hcol.data(), hval.data(), tile_cap, sms, nt);
+    } catch (...) {
+      job_failed = true;
+    }
+  });
 
   // local plan
   phase.next("ls_setup: local matrices and Cholesky factors");
@@ -1444,6 +1462,38 @@ void do_setup(ls_handle* h, const int64_t* row_ptr_in, const int32_t* col_in, co
   if (h->opt.time_kernels)
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
   std::memset(h->pin, 0, sizeof(double) * lsq::S_NSLOT);
+  phase.next("ls_setup: sparse-product copies and autotuning");
+  job.join();
+  if (job_failed) throw LsError(LS_ERR_OOM, "host memory for the sparse-product copies");
+  h->sellA_src.upload(sa.src, st);
+  h->sellB_src.upload(sb.src, st);
+  h->sellA.nslices = sa.nslices;
+  h->sellA_off.upload(sa.off, st); h->sellA_perm.upload(sa.perm, st);
+  h->sellA_col.upload(sa.col, st); h->sellA_val.upload(sa.val, st);
+  h->sellB.nslices = sb.nslices;
+  h->sellB_off.upload(sb.off, st); h->sellB_perm.upload(sb.perm, st);
+  h->sellB_col.upload(sb.col, st); h->sellB_val.upload(sb.val, st);
+  if (nt_ok) {
+    h->nt_lo.upload(nt.lo, st); h->nt_wid.upload(nt.wid, st);
+    h->nt_as0.upload(nt.as0, st); h->nt_bs0.upload(nt.bs0, st);
+    h->nt_aoff.upload(nt.aoff, st); h->nt_acol.upload(nt.acol, st); h->nt_aval.upload(nt.aval, st);
+    h->nt_boff.upload(nt.boff, st); h->nt_brow.upload(nt.brow, st); h->nt_bval.upload(nt.bval, st);
+    h->nt_bcid.upload(nt.bcid, st); h->nt_poff.upload(nt.poff, st);
+    h->nt_asrc.upload(nt.asrc, st); h->nt_bsrc.upload(nt.bsrc, st);
+    h->nt_cb0.upload(nt.cb_t0, st); h->nt_cb1.upload(nt.cb_t1, st);
+    h->nt_part.alloc((size_t)nt.poff[nt.ntiles]);
+    h->nt_tiles = nt.ntiles;
+    h->nt_smem = nt.smem_doubles;
+    const int64_t st6[6] = {nt.ntiles, (int64_t)nt.aval.size(), (int64_t)nt.bval.size(), nt.as0[nt.ntiles],
+                            nt.bs0[nt.ntiles], nt.poff[nt.ntiles]};
+    for (int k = 0; k < 6; ++k) h->nt_stats[k] = st6[k];
+  }
+  CK(cudaStreamSynchronize(st));  // the host copies go out of scope
+  if (h->nt_tiles > 0 && !lsq::normal_tiles_prepare(ntiles(h))) release_normal_tiles(h);
+  if (h->nt_tiles == 0 && h->opt.normal_product == 2)
+    throw LsError(LS_ERR_UNSUPPORTED, "normal_product = 2: the row tiles do not fit a block's shared memory");
+  if (h->opt.equilibrate) refresh_value_copies(h);  // the copies above hold the scaled values
+  autotune_spmv(h);
   {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
