@@ -116,7 +116,9 @@ typedef struct {
                           the factor to TF32.  ls_info.local_kernel reports the choice. */
     int normal_product;/* form of the product C v = A^T (A v): 0 (the default) times both
                           at setup and keeps the faster (the two products alone when
-                          spmv forces a kernel); 1 two products, q = A v then A^T q; 2
+                          spmv forces a kernel, and on batched handles, whose solves
+                          run the multi right-hand-side products); 1 two products,
+                          q = A v then A^T q; 2
                           row tiles: A is cut into tiles of consecutive rows whose
                           entries fall in a narrow column window, each tile forms A v
                           for its rows and A^T of that for its window in shared memory
@@ -138,8 +140,10 @@ typedef struct {
                           and solution blocks through distributed shared memory (when
                           twice the subdomain count does not exceed the SM count); 0 (the
                           default) times those that fit at the end of setup and keeps
-                          the fastest (LS_ERR_UNSUPPORTED when a forced one does not
-                          fit).  ls_info.local_config reports it.                      */
+                          the fastest (1 without timing on batched handles, whose solves
+                          run the multi right-hand-side path, and with test_stall);
+                          LS_ERR_UNSUPPORTED when a forced one does not fit.
+                          ls_info.local_config reports it.                             */
 } ls_options;
 
 typedef struct {
